@@ -1,0 +1,172 @@
+/*
+ * tabnet.h -- C ABI of the B300 TabNet inference library (libtabnet.so).
+ *
+ * The paper (Sec. III-B) serves a pre-trained TabNet from a GPU function:
+ * each call takes a batch of records and returns the predictions together
+ * with the feature-attribution masks, the batch size being chosen per call;
+ * the model is loaded into GPU memory once, on cold start.  This library is
+ * that compute core: tabnet_create loads a weight blob into device memory,
+ * tabnet_forward runs the whole TabNet forward pass (Sec. IV-A: n_d = n_a,
+ * several decision steps, sparsemax masks; TabNet of Arik & Pfister 2021)
+ * for `rows` records in hand-written sm_103a kernels on the caller's stream.
+ *
+ * Conventions for every function below:
+ *   - Return value: TABNET_OK (0) or a negative TABNET_ERR_* code.  No C++
+ *     exception and no abort crosses this boundary.  Argument checks are
+ *     synchronous; faults found by a kernel (an out-of-range categorical
+ *     index, a wait that ran out) are reported asynchronously through
+ *     tabnet_poll_status.
+ *   - "device pointer" means memory of the model's device (cudaMalloc,
+ *     cudaMallocAsync, or torch tensors); "host pointer" means CPU memory.
+ *   - Streams are passed as `void*` holding a cudaStream_t (NULL = legacy
+ *     default stream).  Calls are stream-ordered and return before the work
+ *     finishes; the caller synchronises.
+ *   - All floating-point tensors are row-major float32, integers int32.
+ *   - A handle may be used from several host threads and streams at once
+ *     for forward calls (the weights are read-only); create/destroy must not
+ *     race with other calls on the same handle.
+ */
+#ifndef TABNET_H
+#define TABNET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TABNET_ABI_VERSION 1
+
+/* Status codes. */
+#define TABNET_OK                    0
+#define TABNET_ERR_ARG              -1  /* null pointer, negative size, misaligned buffer */
+#define TABNET_ERR_BLOB_MAGIC       -2  /* blob does not start with the TABN magic */
+#define TABNET_ERR_BLOB_VERSION     -3  /* blob format version not supported */
+#define TABNET_ERR_BLOB_SIZE        -4  /* blob shorter/longer than its header says */
+#define TABNET_ERR_BLOB_HASH        -5  /* payload hash mismatch (corrupt blob) */
+#define TABNET_ERR_UNSUPPORTED_DIMS -6  /* model shape outside the kernels' limits */
+#define TABNET_ERR_CUDA             -7  /* a CUDA runtime call failed (no device, bad stream...) */
+#define TABNET_ERR_OOM              -8  /* device allocation failed */
+#define TABNET_ERR_TIMEOUT          -9  /* a bounded device wait ran out (see poll_status) */
+#define TABNET_ERR_DEVICE           -10 /* poll_status found a device-side fault bit */
+
+/* Device status bits (tabnet_poll_status). */
+#define TABNET_STATUS_CAT_OOB  0x1u  /* a categorical index was outside [0, card): a zero
+                                        embedding row was used for it */
+#define TABNET_STATUS_TIMEOUT  0x2u  /* a bounded barrier wait ran out; outputs of that
+                                        launch are undefined */
+
+/* Arithmetic of the fully connected layers.  In every mode the sparsemax
+ * threshold, the prior, the masks and their aggregation are float32. */
+typedef enum {
+    TABNET_FP32 = 0,      /* float32 FMA everywhere (no TF32) */
+    TABNET_BF16 = 1,      /* bf16 x bf16 -> fp32 tensor-core FCs (tcgen05): every
+                             weight and activation rounded once to bf16 */
+    TABNET_FP8_E4M3 = 2,  /* e4m3 weights with per-output-channel scales, e4m3
+                             activations with per-row scales, fp32 accumulation */
+    TABNET_BF16X3 = 3     /* split bf16 on the same tensor cores: each operand
+                             carried as hi + lo bf16 (lo = bf16(x - hi)), three
+                             bf16 MMAs per K step (hi*hi + hi*lo + lo*hi) into
+                             one fp32 accumulator, accurate sigmoid; about
+                             16 significant bits per operand */
+} tabnet_precision;
+
+/* Model shape, as read from a blob. */
+typedef struct {
+    int32_t n_num;      /* numeric input columns */
+    int32_t n_cat;      /* categorical input columns */
+    int32_t d_emb;      /* D_e: width after embedding = n_num + sum of embedding dims;
+                           width of each per-step mask */
+    int32_t n_feat;     /* D = n_num + n_cat: width of the aggregated mask */
+    int32_t n_d, n_a;   /* decision / attention widths */
+    int32_t n_steps;    /* decision steps (= masks per row) */
+    int32_t n_shared;   /* GLU layers shared by every feature transformer */
+    int32_t n_indep;    /* GLU layers specific to each feature transformer */
+    int32_t n_classes;  /* logits per row */
+    double gamma;       /* prior relaxation */
+    double bn_eps;
+    uint64_t content_hash;  /* payload hash stored in (and checked against) the blob */
+} tabnet_dims;
+
+typedef struct tabnet_model tabnet_model;
+
+/* Returns TABNET_ABI_VERSION. */
+int tabnet_abi_version(void);
+
+/* Validate a weight blob and read its shape without touching a GPU.
+ * blob: host pointer to blob_bytes bytes (format version 1: 96-byte header
+ * then the parameter arrays; written by paper_2510_19689_b300.synth.to_blob).
+ * out: filled on success.  Errors: ARG, BLOB_MAGIC, BLOB_VERSION, BLOB_SIZE,
+ * BLOB_HASH, UNSUPPORTED_DIMS (shape fields out of range). */
+int tabnet_blob_inspect(const void* blob, size_t blob_bytes, tabnet_dims* out);
+
+/* Load a model onto `device` for the given precision (a tabnet_precision).
+ * The blob is validated, its BN statistics are folded into per-channel
+ * scale/shift pairs (input BN also into the embedding tables), its weights
+ * are converted and packed for the kernels of that precision and copied to
+ * device memory owned by the handle.  The blob is only read during the call;
+ * the caller may free it afterwards.  On success *out holds a new handle.
+ * Errors: any of tabnet_blob_inspect, UNSUPPORTED_DIMS (shape outside what
+ * the kernels of that precision handle), CUDA (no such device), OOM. */
+int tabnet_create(const void* blob, size_t blob_bytes, int precision, int device,
+                  tabnet_model** out);
+
+/* Shape of a loaded model.  Errors: ARG. */
+int tabnet_dims_of(const tabnet_model* model, tabnet_dims* out);
+
+/* Precision the handle was created with, or ARG. */
+int tabnet_precision_of(const tabnet_model* model);
+
+/* Batched inference, stream-ordered on `stream`.
+ *   x_num      device, [rows, n_num] float32 (may be NULL when n_num == 0)
+ *   x_cat      device, [rows, n_cat] int32   (may be NULL when n_cat == 0)
+ *   logits     device, [rows, n_classes] float32, raw logits (no softmax)
+ *   step_masks device, [rows, n_steps, d_emb] float32: sparsemax mask of
+ *              every decision step (each sums to 1), or NULL to skip
+ *   agg_mask   device, [rows, n_feat] float32: step masks weighted by each
+ *              step's decision strength, summed over each feature's embedding
+ *              columns and normalised to sum 1 (all zero when every step's
+ *              decision output is zero), or NULL to skip
+ * All buffers are owned by the caller, 4-byte aligned, and must not overlap.
+ * rows == 0 returns TABNET_OK without launching.  Rows are independent:
+ * a row's outputs do not depend on the other rows of the call.
+ * Errors: ARG (null handle or required pointer, rows < 0), CUDA (launch). */
+int tabnet_forward(tabnet_model* model, const float* x_num, const int32_t* x_cat,
+                   int64_t rows, float* logits, float* step_masks, float* agg_mask,
+                   void* stream);
+
+/* Same computation with HOST buffers (pinned or pageable): the inputs are
+ * copied into a device workspace owned by the handle, the forward runs, and
+ * the outputs are copied back, all on `stream`; the call returns after the
+ * stream has finished the copies (synchronous).  This is the paper's
+ * function invocation (records in, predictions and masks out, Sec. III-B)
+ * seen from a host caller.  Workspace grows on demand and is freed by
+ * tabnet_destroy.  Not thread-safe per handle.  Errors: as tabnet_forward,
+ * OOM. */
+int tabnet_forward_host(tabnet_model* model, const float* x_num, const int32_t* x_cat,
+                        int64_t rows, float* logits, float* step_masks, float* agg_mask,
+                        void* stream);
+
+/* Read and clear the handle's device status word (TABNET_STATUS_* bits) after
+ * synchronising `stream`.  *status receives the bits; returns TABNET_OK when
+ * no bit was set, TABNET_ERR_TIMEOUT when the timeout bit was set, else
+ * TABNET_ERR_DEVICE.  Errors: ARG, CUDA. */
+int tabnet_poll_status(tabnet_model* model, void* stream, uint32_t* status);
+
+/* Free the handle and its device memory (synchronises the device first).
+ * NULL is accepted. */
+void tabnet_destroy(tabnet_model* model);
+
+/* Static description of a status code. */
+const char* tabnet_status_string(int code);
+
+/* One-line reason for the last failing call made by this host thread
+ * ("" when none).  The pointer stays valid until the thread's next call. */
+const char* tabnet_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TABNET_H */

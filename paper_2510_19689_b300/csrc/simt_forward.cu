@@ -1,0 +1,255 @@
+// FP32 TabNet forward on the CUDA cores (FFMA, no TF32): the float32
+// precision mode of the library.
+//
+// Layout.  A CTA owns ROWS rows; four consecutive lanes own one row, so the
+// whole life of a row (embedding, every feature transformer, attentive
+// transformer, sparsemax, prior, aggregation) stays inside one warp and the
+// only synchronisation is __syncwarp.  Per-row state lives in shared memory
+// as [column][row] arrays, which makes the four lanes of a row read the
+// same word (broadcast) and different rows hit different banks.  Weights
+// are read through the read-only cache, transposed to [k][n_out] so that the
+// four lanes of a row read consecutive outputs.
+#include <cuda_runtime.h>
+
+#include "../../include/tabnet.h"
+#include "kernel_params.h"
+
+namespace tabnet {
+
+namespace {
+
+constexpr int TPR = 4;  // threads per row
+constexpr float kSqrtHalf = 0.70710678118654752440f;
+
+// The four lanes of one row: rows of a warp leave data-dependent loops
+// (sparsemax) at different iterations, so shuffles name only this group.
+__device__ __forceinline__ unsigned row_mask() { return 0xFu << (threadIdx.x & 28); }
+
+__device__ __forceinline__ float sum4(float v) {
+    const unsigned mk = row_mask();
+    v += __shfl_xor_sync(mk, v, 1);
+    v += __shfl_xor_sync(mk, v, 2);
+    return v;
+}
+
+__device__ __forceinline__ int sum4i(int v) {
+    const unsigned mk = row_mask();
+    v += __shfl_xor_sync(mk, v, 1);
+    v += __shfl_xor_sync(mk, v, 2);
+    return v;
+}
+
+__device__ __forceinline__ float sigmoid_exact(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// One GLU layer for the calling row: nxt[c] = GLU(BN(W cur))[c] (+ residual).
+template <int ROWS>
+__device__ __forceinline__ void glu_layer(const SimtLayer& L, const float* cur, float* nxt,
+                                          bool first, int N, int r, int q) {
+    constexpr int NB = 4;
+    const float* __restrict__ wt = L.wt;
+    const int two_n = 2 * N;
+    for (int c0 = q; c0 < N; c0 += TPR * NB) {
+        float lin[NB], gate[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) { lin[b] = 0.f; gate[b] = 0.f; }
+        for (int k = 0; k < L.k; ++k) {
+            const float x = cur[k * ROWS + r];
+            const float* w = wt + (size_t)k * two_n;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int c = c0 + TPR * b;
+                if (c < N) {
+                    lin[b] = fmaf(__ldg(w + c), x, lin[b]);
+                    gate[b] = fmaf(__ldg(w + N + c), x, gate[b]);
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int c = c0 + TPR * b;
+            if (c < N) {
+                const float ul = fmaf(lin[b], __ldg(L.scale + c), __ldg(L.shift + c));
+                const float ug = fmaf(gate[b], __ldg(L.scale + N + c), __ldg(L.shift + N + c));
+                const float g = ul * sigmoid_exact(ug);
+                nxt[c * ROWS + r] = first ? g : (cur[c * ROWS + r] + g) * kSqrtHalf;
+            }
+        }
+    }
+}
+
+// Feature transformer s on `in` (k = de for the first layer).  Returns the
+// buffer holding its N outputs.
+template <int ROWS>
+__device__ __forceinline__ float* feature_transformer(const SimtParams& p, int s, const float* in,
+                                                      float* b0, float* b1, int r, int q) {
+    const int lpf = p.m.layers_per_ft;
+    const float* cur = in;
+    float* nxt = b1;
+    for (int l = 0; l < lpf; ++l) {
+        glu_layer<ROWS>(p.ft[s * lpf + l], cur, nxt, l == 0, p.m.N, r, q);
+        __syncwarp(row_mask());
+        cur = nxt;
+        nxt = (nxt == b1) ? b0 : b1;
+    }
+    return const_cast<float*>(cur);
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(ROWS * TPR)
+simt_forward_kernel(const SimtParams p, const float* __restrict__ x_num,
+                    const int* __restrict__ x_cat, int64_t rows, float* __restrict__ logits,
+                    float* __restrict__ masks, float* __restrict__ agg_out) {
+    extern __shared__ float sm[];
+    const ModelConsts& m = p.m;
+    const int de = m.de, N = m.N, D = m.d, n_d = m.n_d;
+    const int kmax = de > N ? de : N;
+    float* F = sm;                    // [de]   BN'd embedded input
+    float* P = F + de * ROWS;         // [de]   prior
+    float* Z = P + de * ROWS;         // [de]   attentive output, then the mask
+    float* B0 = Z + de * ROWS;        // [kmax] layer buffer
+    float* B1 = B0 + kmax * ROWS;     // [N]    layer buffer
+    float* AGG = B1 + N * ROWS;       // [D]    aggregate per feature
+    float* ACC = AGG + D * ROWS;      // [n_d]  decision accumulator
+
+    const int r = threadIdx.x / TPR, q = threadIdx.x % TPR;
+    const int64_t row = (int64_t)blockIdx.x * ROWS + r;
+    const bool valid = row < rows;
+
+    // Embedding lookup and input BN (features j = q mod 4).
+    for (int j = q; j < D; j += TPR) {
+        const int c0 = m.feat_col[j];
+        if (j < m.n_num) {
+            const float x = valid ? x_num[row * m.n_num + j] : 0.f;
+            F[c0 * ROWS + r] = fmaf(__ldg(m.s0 + c0), x, __ldg(m.t0 + c0));
+        } else {
+            const int jc = j - m.n_num;
+            const int len = m.feat_len[j];
+            const int idx = valid ? x_cat[row * m.n_cat + jc] : 0;
+            const bool oob = idx < 0 || idx >= m.cat_card[jc];
+            if (oob) atomicOr(m.status, TABNET_STATUS_CAT_OOB);
+            const float* t = m.emb + m.cat_off[jc] + (size_t)(oob ? 0 : idx) * len;
+            for (int e = 0; e < len; ++e)
+                F[(c0 + e) * ROWS + r] = oob ? __ldg(m.t0 + c0 + e) : __ldg(t + e);
+        }
+    }
+    for (int c = q; c < de; c += TPR) P[c * ROWS + r] = 1.f;
+    for (int j = q; j < D; j += TPR) AGG[j * ROWS + r] = 0.f;
+    for (int c = q; c < n_d; c += TPR) ACC[c * ROWS + r] = 0.f;
+    __syncwarp(row_mask());
+
+    float* out = feature_transformer<ROWS>(p, 0, F, B0, B1, r, q);
+
+    for (int i = 0; i < m.n_steps; ++i) {
+        // Attentive transformer: z = BN(W_att a) * P.
+        const SimtLayer& A = p.att[i];
+        for (int c = q; c < de; c += TPR) {
+            float acc = 0.f;
+            for (int k = 0; k < m.n_a; ++k)
+                acc = fmaf(__ldg(A.wt + (size_t)k * de + c), out[(n_d + k) * ROWS + r], acc);
+            const float u = fmaf(acc, __ldg(A.scale + c), __ldg(A.shift + c));
+            Z[c * ROWS + r] = u * P[c * ROWS + r];
+        }
+        __syncwarp(row_mask());
+        // Sparsemax by Michelot's fixed point: tau = (sum_S z - 1) / |S| over
+        // S = {z > tau}, starting from S = all columns, until S stops shrinking.
+        float s = 0.f;
+        for (int c = q; c < de; c += TPR) s += Z[c * ROWS + r];
+        s = sum4(s);
+        float tau = (s - 1.f) / (float)de;
+        int prev = de;
+        for (int it = 0; it < de; ++it) {
+            float ss = 0.f;
+            int cnt = 0;
+            for (int c = q; c < de; c += TPR) {
+                const float z = Z[c * ROWS + r];
+                if (z > tau) { ss += z; ++cnt; }
+            }
+            ss = sum4(ss);
+            cnt = sum4i(cnt);
+            if (cnt == prev || cnt == 0) break;
+            prev = cnt;
+            tau = (ss - 1.f) / (float)cnt;
+        }
+        // Mask, prior update, masked input, mask output.
+        float* mrow = (masks && valid) ? masks + ((size_t)row * m.n_steps + i) * de : nullptr;
+        for (int c = q; c < de; c += TPR) {
+            const float mk = fmaxf(Z[c * ROWS + r] - tau, 0.f);
+            Z[c * ROWS + r] = mk;
+            P[c * ROWS + r] *= (m.gamma - mk);
+            B0[c * ROWS + r] = mk * F[c * ROWS + r];
+            if (mrow) mrow[c] = mk;
+        }
+        __syncwarp(row_mask());
+        out = feature_transformer<ROWS>(p, i + 1, B0, B0, B1, r, q);
+        // Decision output: acc += ReLU(d), eta = sum ReLU(d), agg += eta * M.
+        float eta = 0.f;
+        for (int c = q; c < n_d; c += TPR) {
+            const float dv = fmaxf(out[c * ROWS + r], 0.f);
+            ACC[c * ROWS + r] += dv;
+            eta += dv;
+        }
+        eta = sum4(eta);
+        for (int j = q; j < D; j += TPR) {
+            const int c0 = m.feat_col[j], len = m.feat_len[j];
+            float a = AGG[j * ROWS + r];
+            for (int e = 0; e < len; ++e) a = fmaf(eta, Z[(c0 + e) * ROWS + r], a);
+            AGG[j * ROWS + r] = a;
+        }
+        __syncwarp(row_mask());
+    }
+
+    // Final linear and the normalised aggregate.
+    for (int k = q; k < m.n_classes; k += TPR) {
+        float acc = __ldg(m.bf + k);
+        for (int c = 0; c < n_d; ++c) acc = fmaf(__ldg(m.wf + (size_t)k * n_d + c), ACC[c * ROWS + r], acc);
+        if (valid) logits[(size_t)row * m.n_classes + k] = acc;
+    }
+    float tot = 0.f;
+    for (int j = q; j < D; j += TPR) tot += AGG[j * ROWS + r];
+    tot = sum4(tot);
+    if (agg_out && valid) {
+        const float inv = tot > 0.f ? 1.f / tot : 0.f;
+        for (int j = q; j < D; j += TPR)
+            agg_out[(size_t)row * D + j] = tot > 0.f ? AGG[j * ROWS + r] * inv : 0.f;
+    }
+}
+
+}  // namespace
+
+size_t simt_smem_bytes(const ModelConsts& m, int rows_per_cta) {
+    const int kmax = m.de > m.N ? m.de : m.N;
+    return (size_t)(3 * m.de + kmax + m.N + m.d + m.n_d) * rows_per_cta * sizeof(float);
+}
+
+// Largest rows-per-CTA in {32, 16, 8} whose shared memory fits, 0 if none.
+int simt_pick_rows(const ModelConsts& m, size_t smem_limit) {
+    for (int r : {32, 16, 8})
+        if (simt_smem_bytes(m, r) <= smem_limit) return r;
+    return 0;
+}
+
+cudaError_t simt_configure(int rows_per_cta, size_t smem) {
+    switch (rows_per_cta) {
+        case 32: return cudaFuncSetAttribute(simt_forward_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 16: return cudaFuncSetAttribute(simt_forward_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 8:  return cudaFuncSetAttribute(simt_forward_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t simt_launch(const SimtParams& p, int rows_per_cta, const float* x_num, const int* x_cat,
+                        int64_t rows, float* logits, float* masks, float* agg, cudaStream_t stream) {
+    const size_t smem = simt_smem_bytes(p.m, rows_per_cta);
+    const int64_t grid = (rows + rows_per_cta - 1) / rows_per_cta;
+    if (grid > 0x7fffffff) return cudaErrorInvalidValue;
+    const dim3 block(rows_per_cta * TPR);
+    switch (rows_per_cta) {
+        case 32: simt_forward_kernel<32><<<(unsigned)grid, block, smem, stream>>>(p, x_num, x_cat, rows, logits, masks, agg); break;
+        case 16: simt_forward_kernel<16><<<(unsigned)grid, block, smem, stream>>>(p, x_num, x_cat, rows, logits, masks, agg); break;
+        case 8:  simt_forward_kernel<8><<<(unsigned)grid, block, smem, stream>>>(p, x_num, x_cat, rows, logits, masks, agg); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tabnet

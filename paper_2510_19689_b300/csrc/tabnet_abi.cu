@@ -1,0 +1,458 @@
+// The C ABI: argument checks, model loading (parse, BN folding, packing,
+// upload) and kernel dispatch.  No exception crosses the extern "C" edge.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/tabnet.h"
+#include "host_model.h"
+#include "kernel_params.h"
+#include "model_handle.h"
+
+namespace tabnet {
+
+// simt_forward.cu
+size_t simt_smem_bytes(const ModelConsts& m, int rows_per_cta);
+int simt_pick_rows(const ModelConsts& m, size_t smem_limit);
+cudaError_t simt_configure(int rows_per_cta, size_t smem);
+cudaError_t simt_launch(const SimtParams& p, int rows_per_cta, const float* x_num, const int* x_cat,
+                        int64_t rows, float* logits, float* masks, float* agg, cudaStream_t stream);
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& why) {
+    g_last_error = why;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? TABNET_ERR_OOM : TABNET_ERR_CUDA;
+}
+
+// Keeps the caller's current device across a call that needs another one.
+struct DeviceGuard {
+    int prev = -1;
+    bool switched = false;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev) {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) {
+            err = cudaSetDevice(dev);
+            switched = (err == cudaSuccess);
+        }
+    }
+    ~DeviceGuard() {
+        if (switched) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+size_t Arena::add(const void* data, size_t bytes, size_t align) {
+    size_t off = (image.size() + align - 1) / align * align;
+    image.resize(off + bytes, 0);
+    if (data && bytes) std::memcpy(image.data() + off, data, bytes);
+    return off;
+}
+
+namespace {
+
+// Common per-model constants (input BN, embeddings, final linear, tables).
+void build_consts(const HostModel& hm, Arena& a, ConstOffsets& o) {
+    const tabnet_dims& d = hm.dims;
+    std::vector<float> s0, t0;
+    fold_bn(hm.bn0, d.bn_eps, s0, t0);
+    o.s0 = a.add(s0.data(), s0.size() * 4);
+    o.t0 = a.add(t0.data(), t0.size() * 4);
+    // Input BN folded into the tables: emb'[v][e] = s0[c+e] * emb[v][e] + t0[c+e].
+    std::vector<float> emb;
+    std::vector<int> cat_off(d.n_cat);
+    int col = d.n_num;
+    for (int j = 0; j < d.n_cat; ++j) {
+        cat_off[j] = (int)emb.size();
+        const int e = hm.cat_emb_dim[j];
+        for (int v = 0; v < hm.cat_card[j]; ++v)
+            for (int k = 0; k < e; ++k)
+                emb.push_back((float)((double)s0[col + k] * hm.emb[j][(size_t)v * e + k] + t0[col + k]));
+        col += e;
+    }
+    if (emb.empty()) emb.push_back(0.f);
+    o.emb = a.add(emb.data(), emb.size() * 4);
+    if (cat_off.empty()) cat_off.push_back(0);
+    o.cat_off = a.add(cat_off.data(), cat_off.size() * 4);
+    std::vector<int> card(hm.cat_card.begin(), hm.cat_card.end());
+    if (card.empty()) card.push_back(1);
+    o.cat_card = a.add(card.data(), card.size() * 4);
+    std::vector<int> fcol, flen;
+    hm.feature_columns(fcol, flen);
+    o.feat_col = a.add(fcol.data(), fcol.size() * 4);
+    o.feat_len = a.add(flen.data(), flen.size() * 4);
+    o.wf = a.add(hm.final_w.data(), hm.final_w.size() * 4);
+    o.bf = a.add(hm.final_b.data(), hm.final_b.size() * 4);
+}
+
+void fill_consts(const HostModel& hm, const ConstOffsets& o, const uint8_t* base, unsigned* status,
+                 ModelConsts& m) {
+    const tabnet_dims& d = hm.dims;
+    m.n_num = d.n_num; m.n_cat = d.n_cat; m.de = d.d_emb; m.d = d.n_feat;
+    m.n_d = d.n_d; m.n_a = d.n_a; m.N = d.n_d + d.n_a; m.n_steps = d.n_steps;
+    m.layers_per_ft = d.n_shared + d.n_indep; m.n_classes = d.n_classes;
+    m.gamma = (float)d.gamma;
+    m.s0 = (const float*)(base + o.s0);
+    m.t0 = (const float*)(base + o.t0);
+    m.emb = (const float*)(base + o.emb);
+    m.cat_off = (const int*)(base + o.cat_off);
+    m.cat_card = (const int*)(base + o.cat_card);
+    m.feat_col = (const int*)(base + o.feat_col);
+    m.feat_len = (const int*)(base + o.feat_len);
+    m.wf = (const float*)(base + o.wf);
+    m.bf = (const float*)(base + o.bf);
+    m.status = status;
+}
+
+std::vector<float> transpose(const std::vector<float>& w, int rows, int cols) {
+    std::vector<float> t((size_t)rows * cols);
+    for (int r = 0; r < rows; ++r)
+        for (int c = 0; c < cols; ++c) t[(size_t)c * rows + r] = w[(size_t)r * cols + c];
+    return t;
+}
+
+// FP32 path: transposed weights and folded BN per layer; layer tables are
+// patched with device addresses once the arena is allocated.
+struct SimtLayout {
+    struct L { size_t wt, scale, shift; int k, n_out; };
+    std::vector<L> ft, att;
+    size_t ft_table = 0, att_table = 0;
+};
+
+void build_simt(const HostModel& hm, Arena& a, SimtLayout& lay) {
+    const tabnet_dims& d = hm.dims;
+    const int N = d.n_d + d.n_a;
+    std::vector<size_t> shared_wt(d.n_shared);
+    for (int l = 0; l < d.n_shared; ++l) {
+        const int k = (l == 0) ? d.d_emb : N;
+        auto t = transpose(hm.shared_fc[l], 2 * N, k);
+        shared_wt[l] = a.add(t.data(), t.size() * 4, 16);
+    }
+    for (int s = 0; s <= d.n_steps; ++s) {
+        for (int l = 0; l < d.n_shared + d.n_indep; ++l) {
+            GluLayer g = hm.layer(s, l);
+            SimtLayout::L L{};
+            L.k = g.k;
+            L.n_out = 2 * N;
+            if (l < d.n_shared) {
+                L.wt = shared_wt[l];
+            } else {
+                auto t = transpose(*g.w, 2 * N, g.k);
+                L.wt = a.add(t.data(), t.size() * 4, 16);
+            }
+            std::vector<float> sc, sh;
+            fold_bn(*g.bn, d.bn_eps, sc, sh);
+            L.scale = a.add(sc.data(), sc.size() * 4);
+            L.shift = a.add(sh.data(), sh.size() * 4);
+            lay.ft.push_back(L);
+        }
+    }
+    for (int i = 0; i < d.n_steps; ++i) {
+        SimtLayout::L L{};
+        L.k = d.n_a;
+        L.n_out = d.d_emb;
+        auto t = transpose(hm.att_fc[i], d.d_emb, d.n_a);
+        L.wt = a.add(t.data(), t.size() * 4, 16);
+        std::vector<float> sc, sh;
+        fold_bn(hm.att_bn[i], d.bn_eps, sc, sh);
+        L.scale = a.add(sc.data(), sc.size() * 4);
+        L.shift = a.add(sh.data(), sh.size() * 4);
+        lay.att.push_back(L);
+    }
+    lay.ft_table = a.add(nullptr, lay.ft.size() * sizeof(SimtLayer), 16);
+    lay.att_table = a.add(nullptr, lay.att.size() * sizeof(SimtLayer), 16);
+}
+
+void patch_simt(const SimtLayout& lay, Arena& a, const uint8_t* base, SimtParams& p) {
+    auto fill = [&](const std::vector<SimtLayout::L>& src, size_t table) {
+        for (size_t i = 0; i < src.size(); ++i) {
+            SimtLayer L;
+            L.wt = (const float*)(base + src[i].wt);
+            L.scale = (const float*)(base + src[i].scale);
+            L.shift = (const float*)(base + src[i].shift);
+            L.k = src[i].k;
+            L.n_out = src[i].n_out;
+            std::memcpy(a.image.data() + table + i * sizeof(SimtLayer), &L, sizeof(L));
+        }
+    };
+    fill(lay.ft, lay.ft_table);
+    fill(lay.att, lay.att_table);
+    p.ft = (const SimtLayer*)(base + lay.ft_table);
+    p.att = (const SimtLayer*)(base + lay.att_table);
+}
+
+int check_ptr(const void* p, bool required, const char* name) {
+    if (!p) return required ? fail(TABNET_ERR_ARG, std::string(name) + " is NULL") : TABNET_OK;
+    if (reinterpret_cast<uintptr_t>(p) % 4) return fail(TABNET_ERR_ARG, std::string(name) + " is not 4-byte aligned");
+    return TABNET_OK;
+}
+
+}  // namespace
+
+int forward_impl(tabnet_model* m, const float* x_num, const int32_t* x_cat, int64_t rows,
+                 float* logits, float* masks, float* agg, cudaStream_t stream) {
+    cudaError_t e;
+    if (m->precision == TABNET_FP32) {
+        e = simt_launch(m->simt, m->simt_rows, x_num, x_cat, rows, logits, masks, agg, stream);
+    } else {
+        e = tc_launch(m, x_num, x_cat, rows, logits, masks, agg, stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return TABNET_OK;
+}
+
+}  // namespace tabnet
+
+using namespace tabnet;
+
+extern "C" {
+
+int tabnet_abi_version(void) { return TABNET_ABI_VERSION; }
+
+const char* tabnet_last_error(void) { return g_last_error.c_str(); }
+
+const char* tabnet_status_string(int code) {
+    switch (code) {
+        case TABNET_OK: return "ok";
+        case TABNET_ERR_ARG: return "invalid argument";
+        case TABNET_ERR_BLOB_MAGIC: return "blob: bad magic";
+        case TABNET_ERR_BLOB_VERSION: return "blob: unsupported version";
+        case TABNET_ERR_BLOB_SIZE: return "blob: size mismatch";
+        case TABNET_ERR_BLOB_HASH: return "blob: payload hash mismatch";
+        case TABNET_ERR_UNSUPPORTED_DIMS: return "model shape not supported";
+        case TABNET_ERR_CUDA: return "CUDA error";
+        case TABNET_ERR_OOM: return "out of device memory";
+        case TABNET_ERR_TIMEOUT: return "device wait timed out";
+        case TABNET_ERR_DEVICE: return "device reported a fault";
+    }
+    return "unknown status";
+}
+
+int tabnet_blob_inspect(const void* blob, size_t blob_bytes, tabnet_dims* out) {
+    if (!blob || !out) return fail(TABNET_ERR_ARG, "null pointer");
+    try {
+        HostModel hm;
+        std::string why;
+        int rc = parse_blob(blob, blob_bytes, &hm, &why);
+        if (rc != TABNET_OK) return fail(rc, why);
+        *out = hm.dims;
+        return TABNET_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(TABNET_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        return fail(TABNET_ERR_ARG, "unexpected error while parsing");
+    }
+}
+
+int tabnet_create(const void* blob, size_t blob_bytes, int precision, int device, tabnet_model** out) {
+    if (!blob || !out) return fail(TABNET_ERR_ARG, "null pointer");
+    *out = nullptr;
+    if (precision < TABNET_FP32 || precision > TABNET_BF16X3) return fail(TABNET_ERR_ARG, "unknown precision");
+    tabnet_model* m = nullptr;
+    try {
+        m = new tabnet_model();
+        std::string why;
+        int rc = parse_blob(blob, blob_bytes, &m->host, &why);
+        if (rc != TABNET_OK) { delete m; return fail(rc, why); }
+        m->device = device;
+        m->precision = precision;
+        int ndev = 0;
+        cudaError_t e = cudaGetDeviceCount(&ndev);
+        if (e != cudaSuccess || device < 0 || device >= ndev) {
+            delete m;
+            return fail(TABNET_ERR_CUDA, e != cudaSuccess ? std::string("no CUDA device: ") + cudaGetErrorString(e)
+                                                          : std::string("device ordinal out of range"));
+        }
+        DeviceGuard guard(device);
+        if (guard.err != cudaSuccess) { delete m; return cuda_fail(guard.err, "cudaSetDevice"); }
+        cudaDeviceProp prop;
+        if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) { delete m; return cuda_fail(e, "cudaGetDeviceProperties"); }
+        if (prop.major != 10 || prop.minor != 3) {
+            delete m;
+            return fail(TABNET_ERR_CUDA, "kernels are built for sm_103a (B300); device is sm_" +
+                                             std::to_string(prop.major) + std::to_string(prop.minor));
+        }
+        m->num_sms = prop.multiProcessorCount;
+        m->smem_optin = prop.sharedMemPerBlockOptin;
+
+        Arena arena;
+        build_consts(m->host, arena, m->consts_off);
+        SimtLayout simt_lay;
+        if (precision == TABNET_FP32) {
+            build_simt(m->host, arena, simt_lay);
+        } else {
+            rc = tc_build(m, arena, &why);
+            if (rc != TABNET_OK) { delete m; return fail(rc, why); }
+        }
+        if ((e = cudaMalloc(&m->d_arena, arena.image.size())) != cudaSuccess) {
+            int r2 = cuda_fail(e, "cudaMalloc(weights)");
+            delete m;
+            return r2;
+        }
+        if ((e = cudaMalloc(&m->d_status, 4 * sizeof(unsigned))) != cudaSuccess) {
+            int r2 = cuda_fail(e, "cudaMalloc(status)");
+            cudaFree(m->d_arena);
+            delete m;
+            return r2;
+        }
+        const uint8_t* base = static_cast<const uint8_t*>(m->d_arena);
+        fill_consts(m->host, m->consts_off, base, m->d_status, m->consts);
+        if (precision == TABNET_FP32) {
+            m->simt.m = m->consts;
+            patch_simt(simt_lay, arena, base, m->simt);
+            m->simt_rows = simt_pick_rows(m->consts, m->smem_optin);
+            if (m->simt_rows == 0) {
+                tabnet_destroy(m);
+                return fail(TABNET_ERR_UNSUPPORTED_DIMS, "model state does not fit in shared memory");
+            }
+            if ((e = simt_configure(m->simt_rows, simt_smem_bytes(m->consts, m->simt_rows))) != cudaSuccess) {
+                tabnet_destroy(m);
+                return cuda_fail(e, "cudaFuncSetAttribute");
+            }
+        } else {
+            rc = tc_patch(m, arena, base, &why);
+            if (rc != TABNET_OK) { tabnet_destroy(m); return fail(rc, why); }
+        }
+        m->arena_bytes = arena.image.size();
+        if ((e = cudaMemcpy(m->d_arena, arena.image.data(), arena.image.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemset(m->d_status, 0, 4 * sizeof(unsigned))) != cudaSuccess) {
+            tabnet_destroy(m);
+            return cuda_fail(e, "upload");
+        }
+        *out = m;
+        return TABNET_OK;
+    } catch (const std::bad_alloc&) {
+        delete m;
+        return fail(TABNET_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        delete m;
+        return fail(TABNET_ERR_ARG, "unexpected error in create");
+    }
+}
+
+int tabnet_dims_of(const tabnet_model* m, tabnet_dims* out) {
+    if (!m || !out) return fail(TABNET_ERR_ARG, "null pointer");
+    *out = m->host.dims;
+    return TABNET_OK;
+}
+
+int tabnet_precision_of(const tabnet_model* m) {
+    if (!m) return fail(TABNET_ERR_ARG, "null pointer");
+    return m->precision;
+}
+
+int tabnet_forward(tabnet_model* m, const float* x_num, const int32_t* x_cat, int64_t rows,
+                   float* logits, float* step_masks, float* agg_mask, void* stream) {
+    if (!m) return fail(TABNET_ERR_ARG, "null model");
+    if (rows < 0) return fail(TABNET_ERR_ARG, "rows < 0");
+    if (rows == 0) return TABNET_OK;
+    const tabnet_dims& d = m->host.dims;
+    int rc;
+    if ((rc = check_ptr(x_num, d.n_num > 0, "x_num")) || (rc = check_ptr(x_cat, d.n_cat > 0, "x_cat")) ||
+        (rc = check_ptr(logits, true, "logits")) || (rc = check_ptr(step_masks, false, "step_masks")) ||
+        (rc = check_ptr(agg_mask, false, "agg_mask")))
+        return rc;
+    DeviceGuard guard(m->device);
+    if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+    return forward_impl(m, x_num, x_cat, rows, logits, step_masks, agg_mask, (cudaStream_t)stream);
+}
+
+int tabnet_forward_host(tabnet_model* m, const float* x_num, const int32_t* x_cat, int64_t rows,
+                        float* logits, float* step_masks, float* agg_mask, void* stream) {
+    if (!m) return fail(TABNET_ERR_ARG, "null model");
+    if (rows < 0) return fail(TABNET_ERR_ARG, "rows < 0");
+    if (rows == 0) return TABNET_OK;
+    const tabnet_dims& d = m->host.dims;
+    int rc;
+    if ((rc = check_ptr(x_num, d.n_num > 0, "x_num")) || (rc = check_ptr(x_cat, d.n_cat > 0, "x_cat")) ||
+        (rc = check_ptr(logits, true, "logits")) || (rc = check_ptr(step_masks, false, "step_masks")) ||
+        (rc = check_ptr(agg_mask, false, "agg_mask")))
+        return rc;
+    DeviceGuard guard(m->device);
+    if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t b_num = (size_t)rows * d.n_num * 4, b_cat = (size_t)rows * d.n_cat * 4;
+    const size_t b_lg = (size_t)rows * d.n_classes * 4, b_mk = (size_t)rows * d.n_steps * d.d_emb * 4;
+    const size_t b_ag = (size_t)rows * d.n_feat * 4;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t need = up(b_num) + up(b_cat) + up(b_lg) + (step_masks ? up(b_mk) : 0) + (agg_mask ? up(b_ag) : 0);
+    cudaError_t e;
+    if (need > m->ws_bytes) {
+        if (m->d_ws) {
+            cudaStreamSynchronize(s);
+            cudaFree(m->d_ws);
+            m->d_ws = nullptr;
+            m->ws_bytes = 0;
+        }
+        if ((e = cudaMalloc(&m->d_ws, need)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+        m->ws_bytes = need;
+    }
+    uint8_t* w = static_cast<uint8_t*>(m->d_ws);
+    float* dn = (float*)w;            w += up(b_num);
+    int32_t* dc = (int32_t*)w;        w += up(b_cat);
+    float* dl = (float*)w;            w += up(b_lg);
+    float* dm = step_masks ? (float*)w : nullptr; if (step_masks) w += up(b_mk);
+    float* da = agg_mask ? (float*)w : nullptr;
+    if (b_num && (e = cudaMemcpyAsync(dn, x_num, b_num, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(e, "H2D x_num");
+    if (b_cat && (e = cudaMemcpyAsync(dc, x_cat, b_cat, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(e, "H2D x_cat");
+    rc = forward_impl(m, b_num ? dn : nullptr, b_cat ? dc : nullptr, rows, dl, dm, da, s);
+    if (rc != TABNET_OK) return rc;
+    if ((e = cudaMemcpyAsync(logits, dl, b_lg, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "D2H logits");
+    if (dm && (e = cudaMemcpyAsync(step_masks, dm, b_mk, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "D2H masks");
+    if (da && (e = cudaMemcpyAsync(agg_mask, da, b_ag, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "D2H agg");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return TABNET_OK;
+}
+
+int tabnet_poll_status(tabnet_model* m, void* stream, uint32_t* status) {
+    if (!m || !status) return fail(TABNET_ERR_ARG, "null pointer");
+    DeviceGuard guard(m->device);
+    if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned w[4] = {0, 0, 0, 0};
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if ((e = cudaMemcpy(w, m->d_status, sizeof(w), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e, "read status");
+    if ((e = cudaMemset(m->d_status, 0, sizeof(w))) != cudaSuccess) return cuda_fail(e, "clear status");
+    const unsigned v = w[0];
+    *status = v;
+    if (v & TABNET_STATUS_TIMEOUT) {
+        // word 1: where the first wait ran out (kind << 24 | index), word 2: CTA
+        char buf[160];
+        std::snprintf(buf, sizeof(buf), "a bounded device wait ran out (kind %u, index %u, block %u)", w[1] >> 24,
+                      w[1] & 0xFFFFFFu, w[2]);
+        return fail(TABNET_ERR_TIMEOUT, buf);
+    }
+    if (v) return fail(TABNET_ERR_DEVICE, "device status bits set");
+    return TABNET_OK;
+}
+
+void tabnet_destroy(tabnet_model* m) {
+    if (!m) return;
+    {
+        DeviceGuard guard(m->device);
+        cudaDeviceSynchronize();
+        if (m->d_arena) cudaFree(m->d_arena);
+        if (m->d_status) cudaFree(m->d_status);
+        if (m->d_ws) cudaFree(m->d_ws);
+        tc_release(m);
+    }
+    delete m;
+}
+
+}  // extern "C"

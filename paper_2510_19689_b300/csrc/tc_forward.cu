@@ -1,0 +1,923 @@
+// TabNet forward with the fully connected layers on the 5th-generation
+// tensor cores (tcgen05, sm_103a): the bf16 and split-bf16 precision modes.
+//
+// One CTA owns a tile of 128 rows for the whole forward pass: the embedding
+// and input BN, the step-0 feature transformer, then per decision step the
+// attentive FC, sparsemax, prior update, masked input and the step's feature
+// transformer, and finally the logits and the aggregated mask (TabNet as
+// deployed in Sec. IV-A; masks as returned per call, Sec. III-B).  Only the
+// inputs, the weights and the outputs touch global memory.
+//
+//   * Every FC is a 128 x n x K tcgen05.mma chain (M = 128 rows; n = 2N for a
+//     GLU layer, the padded mask width for the attentive layer) reading the
+//     activations (A) and the layer's weights (B) from shared memory in the
+//     128-byte-swizzled K-major layout and accumulating in fp32 in tensor
+//     memory (TMEM lane = row).  In split mode both operands are carried as
+//     hi + lo bf16 pairs and each K step issues hi*hi, hi*lo and lo*hi.
+//   * Weights stream from L2 through a ring of shared-memory slots filled by
+//     1-D bulk async copies (TMA engine), one 64-wide K block (hi or lo) per
+//     slot, pre-swizzled by the host.  Thread 0 issues copies and MMAs; each
+//     slot has a "full" barrier (copy landed) and an "empty" barrier (the
+//     MMAs that read it completed, via tcgen05.commit).
+//   * Epilogue threads read the accumulator with tcgen05.ld (thread = row),
+//     apply the folded BN scale/shift, the GLU and the sqrt(0.5) residual
+//     (kept in fp32 registers), and write the next layer's A operand straight
+//     into shared memory.
+//   * Sparsemax runs in fp32, row per thread, by Michelot's fixed point on
+//     the threshold (the sort-free exact projection); the prior P lives in
+//     TMEM in fp32, the current mask in TMEM as fp16 pairs (read again only
+//     for the aggregate), the per-feature aggregate in shared memory.
+//   * With NWG = 2 two warpgroups split the columns of each row and combine
+//     partial sums through shared memory.
+//
+// Every wait is bounded: a wait that runs out sets TABNET_STATUS_TIMEOUT,
+// the CTA stops at the next barrier, drains its copies and MMAs, frees its
+// TMEM and exits.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "../../include/tabnet.h"
+#include "model_handle.h"
+#include "tc_ptx.cuh"
+
+namespace tabnet {
+
+#ifdef TABNET_TRACE
+unsigned* tabnet_debug_trace_ptr();
+#endif
+
+namespace {
+
+constexpr uint64_t kWaitLimit = 1000000000ull;  // 1 s per wait
+constexpr float kSqrtHalf = 0.70710678118654752440f;
+constexpr int kMaxClasses = 8;
+constexpr int kZregChunks = 3;  // sparsemax input kept in registers up to 3 x 16 columns per thread
+
+#ifdef TABNET_TRACE
+#define TC_TRACE(i, v)                                                          \
+    do {                                                                        \
+        if (p.trace && blockIdx.x == 0) {                                       \
+            reinterpret_cast<volatile unsigned*>(p.trace)[(i)] = (unsigned)(v); \
+            __threadfence_system();                                             \
+        }                                                                       \
+    } while (0)
+#else
+#define TC_TRACE(i, v) \
+    do {               \
+    } while (0)
+#endif
+
+// Record a wait that ran out: the status bit, and the first location.
+__device__ __forceinline__ void note_timeout(unsigned* status, unsigned kind, unsigned index) {
+    atomicOr(status, TABNET_STATUS_TIMEOUT);
+    if (atomicCAS(status + 1, 0u, (kind << 24) | (index & 0xFFFFFFu)) == 0u) status[2] = blockIdx.x;
+}
+
+// sigmoid(x) = 1 / (1 + 2^(-x log2 e)) with the ex2/rcp approximations
+// (about 2^-21 relative): the split mode's gate.
+__device__ __forceinline__ float sigmoid_accurate(float x) {
+    float e, r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x * -1.4426950408889634f));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
+    return r;
+}
+
+// sigmoid(x) = (1 + tanh(x / 2)) / 2 with tanh.approx (about 2^-11): the
+// plain bf16 mode's gate, one MUFU operation.
+__device__ __forceinline__ float sigmoid_fast(float x) {
+    return fmaf(0.5f, ptx::tanh_approx(0.5f * x), 0.5f);
+}
+
+// Byte offset of 16-byte unit q (0..7) of row r inside a 128-row x 64-column
+// bf16 block in the 128B-swizzled K-major layout.
+__device__ __forceinline__ uint32_t sw128_off(int r, int q) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((q ^ (r & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Row r, K columns [16 ch, 16 ch + 16) of the A operand: bf16(v), and in
+// split mode also bf16(v - bf16(v)) into the low-half buffer.
+template <bool SPLIT>
+__device__ __forceinline__ void store_a16(uint8_t* sA, uint8_t* sAlo, int r, int ch, const float (&v)[16]) {
+    uint32_t w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
+    const uint32_t o0 = (uint32_t)((ch >> 2) * 16384) + sw128_off(r, (ch & 3) * 2);
+    const uint32_t o1 = (uint32_t)((ch >> 2) * 16384) + sw128_off(r, (ch & 3) * 2 + 1);
+    *reinterpret_cast<uint4*>(sA + o0) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(sA + o1) = make_uint4(w[4], w[5], w[6], w[7]);
+    if constexpr (SPLIT) {
+        uint32_t l[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[j]);
+            const float2 hf = __bfloat1622float2(h);
+            l[j] = pack_bf16(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+        }
+        *reinterpret_cast<uint4*>(sAlo + o0) = make_uint4(l[0], l[1], l[2], l[3]);
+        *reinterpret_cast<uint4*>(sAlo + o1) = make_uint4(l[4], l[5], l[6], l[7]);
+    }
+}
+
+template <int N, int NWG, bool SPLIT, bool ZREG>
+__global__ void __launch_bounds__(128 * NWG, 1)
+tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* __restrict__ x_cat,
+                  int64_t rows, float* __restrict__ logits, float* __restrict__ masks,
+                  float* __restrict__ agg_out) {
+    constexpr int THREADS = 128 * NWG;
+    constexpr int CPW = N / NWG;  // GLU output columns per warpgroup
+    constexpr int RCH = CPW / 16;  // 16-column chunks per thread
+    constexpr int PARTS = SPLIT ? 2 : 1;  // weight chunks per 64-wide K block
+    static_assert(CPW % 16 == 0, "each warpgroup takes whole 16-column chunks");
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const ModelConsts& m = p.m;
+    const int tid = threadIdx.x, wg = tid >> 7, lt = tid & 127, warp = tid >> 5;
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+
+    uint8_t* sA = smem + p.sm.a_hi;
+    uint8_t* sAlo = SPLIT ? smem + p.sm.a_lo : nullptr;
+    float* sAgg = reinterpret_cast<float*>(smem + p.sm.agg);
+    float2* sX = reinterpret_cast<float2*>(smem + (p.sm.xch >= 0 ? p.sm.xch : 0));
+    float* sWf = reinterpret_cast<float*>(smem + p.sm.wf);
+    float* sF = p.sm.fcache >= 0 ? reinterpret_cast<float*>(smem + p.sm.fcache) : nullptr;
+    const float* epi = p.sm.epi >= 0 ? reinterpret_cast<const float*>(smem + p.sm.epi) : p.epi;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.sm.bar);
+    const int S = p.n_slots;
+    volatile uint32_t* sTmem = reinterpret_cast<volatile uint32_t*>(bars + 2 * S + 1);
+    volatile int* sAbort = reinterpret_cast<volatile int*>(bars + 2 * S + 2);
+    const uint32_t bar_full = ptx::smem_u32(bars);
+    const uint32_t bar_empty = ptx::smem_u32(bars + S);
+    const uint32_t bar_acc = ptx::smem_u32(bars + 2 * S);
+    const uint32_t a_base = ptx::smem_u32(sA);
+    const uint32_t alo_base = SPLIT ? ptx::smem_u32(sAlo) : 0u;
+    const uint32_t ring_base = ptx::smem_u32(smem + p.sm.ring);
+
+    if (tid == 0) {
+        for (int s = 0; s < 2 * S + 1; ++s) ptx::mbar_init(bar_full + 8 * s, 1);
+        *sAbort = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 0) {
+        ptx::tmem_alloc(ptx::smem_u32((const void*)sTmem), (uint32_t)p.tmem_cols);
+        ptx::tmem_relinquish();
+    }
+    // model constants staged once per CTA
+    for (int i = tid; i < m.n_classes * m.n_d; i += THREADS) sWf[i] = __ldg(m.wf + i);
+    if (p.sm.epi >= 0)
+        for (int i = tid; i < p.epi_floats / 4; i += THREADS)
+            reinterpret_cast<float4*>(smem + p.sm.epi)[i] = __ldg(reinterpret_cast<const float4*>(p.epi) + i);
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *sTmem;
+    TC_TRACE(64 + tid / 32, 2);
+    const uint32_t t_acc = tmem + lane_off;
+    const uint32_t t_p = t_acc + (uint32_t)p.tm_p;
+    const uint32_t t_m = t_acc + (uint32_t)p.tm_m;
+
+    const int64_t my_tiles =
+        (int64_t)blockIdx.x < p.num_tiles ? (p.num_tiles - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t total_chunks = my_tiles * p.chunks_per_tile;
+    int64_t g_issue = 0, g_cons = 0;   // thread 0 only
+    bool acc_outstanding = false;      // thread 0 only
+    uint32_t acc_phase = 0;
+    int xc = 0;
+    int lc = 0;  // layers run by this CTA
+
+    // Thread 0: start the copy of chunk g_issue once its slot is free.
+    auto issue_next = [&]() -> bool {
+        const int64_t g = g_issue;
+        const int slot = (int)(g % S);
+        if (g >= S && !ptx::mbar_wait(bar_empty + 8 * slot, (uint32_t)(((g / S) - 1) & 1), kWaitLimit)) {
+            note_timeout(m.status, 5, (unsigned)g);
+            return false;
+        }
+        const uint2 ck = p.chunks[g % p.chunks_per_tile];
+        ptx::mbar_arrive_expect_tx(bar_full + 8 * slot, ck.y);
+        ptx::bulk_g2s(ring_base + (uint32_t)(slot * p.slot_bytes), p.wbase + ck.x, ck.y, bar_full + 8 * slot);
+        ++g_issue;
+        return true;
+    };
+    if (tid == 0)
+        while (g_issue < total_chunks && g_issue < S) issue_next();
+
+    // Publish this thread's A-operand writes and TMEM reads, then let thread 0
+    // run one layer's MMA chain (kblocks 64-wide K blocks, kb K steps of 16)
+    // and wait for the accumulator.  Returns false when the CTA has to stop.
+    auto run_mma = [&](int kblocks, int kb, uint32_t idesc) -> bool {
+        ptx::fence_proxy_async();
+        ptx::tc_fence_before();
+        __syncthreads();
+        if (*sAbort) return false;
+        if (tid == 0) {
+            ptx::tc_fence_after();
+            int kk = 0;
+            bool ok = true;
+            for (int b = 0; b < kblocks && ok; ++b) {
+                const int64_t g = g_cons;
+                while (ok && g_issue < g + PARTS) ok = issue_next();
+                for (int part = 0; part < PARTS && ok; ++part) {
+                    const int64_t gp = g + part;
+                    if (!ptx::mbar_wait(bar_full + 8 * (int)(gp % S), (uint32_t)((gp / S) & 1), kWaitLimit)) {
+                        note_timeout(m.status, 1, (unsigned)gp);
+                        ok = false;
+                    }
+                }
+                if (!ok) break;
+                const uint32_t b_hi = ring_base + (uint32_t)((int)(g % S) * p.slot_bytes);
+                const uint32_t b_lo = ring_base + (uint32_t)((int)((g + 1) % S) * p.slot_bytes);
+                const uint32_t a_hi = a_base + (uint32_t)(b * 16384);
+                const uint32_t a_lo = alo_base + (uint32_t)(b * 16384);
+#pragma unroll 1
+                for (int k4 = 0; k4 < 4 && kk < kb; ++k4, ++kk) {
+                    ptx::mma_f16(tmem, ptx::sw128_desc(a_hi + 32 * k4), ptx::sw128_desc(b_hi + 32 * k4), idesc,
+                                 kk > 0 ? 1u : 0u);
+                    if constexpr (SPLIT) {
+                        ptx::mma_f16(tmem, ptx::sw128_desc(a_hi + 32 * k4), ptx::sw128_desc(b_lo + 32 * k4), idesc, 1u);
+                        ptx::mma_f16(tmem, ptx::sw128_desc(a_lo + 32 * k4), ptx::sw128_desc(b_hi + 32 * k4), idesc, 1u);
+                    }
+                }
+                for (int part = 0; part < PARTS; ++part) ptx::mma_commit(bar_empty + 8 * (int)((g + part) % S));
+                g_cons += PARTS;
+            }
+            ptx::mma_commit(bar_acc);
+            acc_outstanding = true;
+            if (!ok) *sAbort = 1;
+        }
+        const bool got = ptx::mbar_wait(bar_acc, acc_phase, kWaitLimit);
+        acc_phase ^= 1;
+        ptx::tc_fence_after();
+        if (!got) {
+            *sAbort = 1;
+            note_timeout(m.status, 2, (unsigned)lc);
+        }
+        ++lc;
+        if (tid == 0) {
+            if (got) acc_outstanding = false;
+            // every MMA so far has completed: refill the free slots
+            if (!*sAbort)
+                while (g_issue < total_chunks && g_issue < g_cons + S)
+                    if (!issue_next()) { *sAbort = 1; break; }
+        }
+        return true;
+    };
+
+    // Sum of (a, b) over the warpgroups sharing a row, same order everywhere.
+    auto xsum = [&](float a, float b) -> float2 {
+        if constexpr (NWG == 1) {
+            return make_float2(a, b);
+        } else {
+            float2* slot = sX + (xc & 1) * 256;
+            slot[wg * 128 + lt] = make_float2(a, b);
+            ptx::named_bar_sync(1, THREADS);
+            const float2 o = slot[(wg ^ 1) * 128 + lt];
+            ++xc;
+            return wg == 0 ? make_float2(a + o.x, b + o.y) : make_float2(o.x + a, o.y + b);
+        }
+    };
+
+    const int de = m.de, dch = p.dp / 16, n_d = m.n_d, n_cls = m.n_classes;
+    const float gamma = m.gamma;
+    const uint32_t idesc_ft = ptx::idesc_bf16(2 * N);
+    const uint32_t idesc_att = ptx::idesc_bf16(p.dp);
+    const int lpf = m.layers_per_ft;
+    const int n_ft_layers = (m.n_steps + 1) * lpf;
+
+    bool alive = true;
+    for (int64_t tile = blockIdx.x; tile < p.num_tiles && alive; tile += gridDim.x) {
+        const int64_t row = tile * 128 + lt;
+        const bool valid = row < rows;
+
+        // Embedded, BN'd input value of column c for this row.
+        auto f_value = [&](int c, bool check) -> float {
+            const int2 ci = __ldg(p.col_info + c);
+            if (ci.x == -1) {
+                const float x = valid ? __ldg(x_num + row * m.n_num + ci.y) : 0.f;
+                return fmaf(__ldg(m.s0 + c), x, __ldg(m.t0 + c));
+            }
+            if (ci.x >= 0) {
+                const int idx = valid ? __ldg(x_cat + row * m.n_cat + ci.x) : 0;
+                if (idx < 0 || idx >= __ldg(m.cat_card + ci.x)) {
+                    if (check) atomicOr(m.status, TABNET_STATUS_CAT_OOB);
+                    return __ldg(m.t0 + c);
+                }
+                const int len = __ldg(m.feat_len + m.n_num + ci.x);
+                return __ldg(m.emb + __ldg(m.cat_off + ci.x) + (size_t)idx * len + ci.y);
+            }
+            return 0.f;
+        };
+
+        // ---- tile start: f -> A (K = dp), P = 1, aggregate = 0
+        for (int ch = wg; ch < dch; ch += NWG) {
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                v[j] = f_value(ch * 16 + j, valid);
+                if (sF) sF[(ch * 16 + j) * 128 + lt] = v[j];
+            }
+            store_a16<SPLIT>(sA, sAlo, lt, ch, v);
+            uint32_t ones[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) ones[j] = 0x3f800000u;
+            ptx::tmem_st16(t_p + ch * 16, ones);
+        }
+        for (int j = wg; j < m.d; j += NWG) sAgg[j * 128 + lt] = 0.f;
+        ptx::tmem_wait_st();
+        float lacc[kMaxClasses];
+#pragma unroll
+        for (int k = 0; k < kMaxClasses; ++k) lacc[k] = 0.f;
+        float res[RCH][16];
+
+        for (int s = 0; s <= m.n_steps && alive; ++s) {
+            if (s > 0) {
+                // ---- attentive transformer of step s: z = (W_att a) * scale + shift, times P
+                if (!run_mma(p.kn_blocks, N / 16, idesc_att)) { alive = false; break; }
+                const float* asc = epi + n_ft_layers * 4 * N + (s - 1) * 2 * p.dp;
+                const float* ash = asc + p.dp;
+                auto load_z = [&](int ch, float (&z)[16], uint32_t (&pr)[16]) {
+                    uint32_t acc[16];
+                    ptx::tmem_ld16(t_acc + ch * 16, acc);
+                    ptx::tmem_ld16(t_p + ch * 16, pr);
+                    ptx::tmem_wait_ld(acc, pr);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 a = *reinterpret_cast<const float4*>(asc + ch * 16 + 4 * q);
+                        const float4 b = *reinterpret_cast<const float4*>(ash + ch * 16 + 4 * q);
+                        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const int j = 4 * q + t;
+                            z[j] = (ch * 16 + j < de)
+                                       ? fmaf(__uint_as_float(acc[j]), av[t], bv[t]) * __uint_as_float(pr[j])
+                                       : -INFINITY;
+                        }
+                    }
+                };
+                // Sparsemax: Michelot's fixed point tau = (sum_{z > tau} z - 1) / #{z > tau},
+                // from tau = (sum z - 1) / de, until the support stops shrinking.
+                float zr[ZREG ? kZregChunks : 1][16];
+                float zs = 0.f;
+                if constexpr (ZREG) {
+#pragma unroll
+                    for (int il = 0; il < kZregChunks; ++il) {
+                        const int ch = wg + il * NWG;
+                        if (ch < dch) {
+                            uint32_t pr[16];
+                            load_z(ch, zr[il], pr);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (ch * 16 + j < de) zs += zr[il][j];
+                        }
+                    }
+                } else {
+                    for (int ch = wg; ch < dch; ch += NWG) {
+                        float z[16];
+                        uint32_t pr[16];
+                        load_z(ch, z, pr);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (ch * 16 + j < de) zs += z[j];
+                    }
+                }
+                float tau = (xsum(zs, 0.f).x - 1.f) / (float)de;
+                int prev = de;
+                bool done = false;
+                // Rows converge after different numbers of passes, but TMEM
+                // loads and the warpgroup exchange are collective: every thread
+                // runs every pass until the last row of its warp (CTA) has
+                // converged; a converged row keeps its threshold.
+                for (int it = 0; it < de; ++it) {
+                    float ss = 0.f, cnt = 0.f;
+                    if constexpr (ZREG) {
+#pragma unroll
+                        for (int il = 0; il < kZregChunks; ++il) {
+                            if (wg + il * NWG < dch) {
+#pragma unroll
+                                for (int j = 0; j < 16; ++j)
+                                    if (zr[il][j] > tau) { ss += zr[il][j]; cnt += 1.f; }
+                            }
+                        }
+                    } else {
+                        for (int ch = wg; ch < dch; ch += NWG) {
+                            float z[16];
+                            uint32_t pr[16];
+                            load_z(ch, z, pr);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (z[j] > tau) { ss += z[j]; cnt += 1.f; }
+                        }
+                    }
+                    const float2 t = xsum(ss, cnt);
+                    if (!done) {
+                        const int c = (int)t.y;
+                        if (c == prev || c == 0) {
+                            done = true;
+                        } else {
+                            prev = c;
+                            tau = (t.x - 1.f) / t.y;
+                        }
+                    }
+                    if constexpr (NWG == 1) {
+                        if (!__any_sync(0xffffffffu, !done)) break;
+                    } else {
+                        if (!ptx::named_bar_or(2, THREADS, !done)) break;
+                    }
+                }
+                TC_TRACE(128 + tid / 32, 4000 + lc);
+                // Mask, prior, masked input (A for the step's first FC), outputs.
+                float* mrow = (masks && valid) ? masks + ((size_t)row * m.n_steps + (s - 1)) * de : nullptr;
+#pragma unroll 1
+                for (int il = 0; wg + il * NWG < dch; ++il) {
+                    const int ch = wg + il * NWG;
+                    float z[16];
+                    uint32_t pr[16];
+                    if constexpr (ZREG) {
+                        ptx::tmem_ld16(t_p + ch * 16, pr);
+                        ptx::tmem_wait_ld(pr);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            float zz = zr[0][j];
+#pragma unroll
+                            for (int q = 1; q < kZregChunks; ++q)
+                                if (il == q) zz = zr[q][j];
+                            z[j] = zz;
+                        }
+                    } else {
+                        load_z(ch, z, pr);
+                    }
+                    float mk[16], v[16];
+                    uint32_t pn[16], mh[8];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        mk[j] = fmaxf(z[j] - tau, 0.f);
+                        pn[j] = __float_as_uint(__uint_as_float(pr[j]) * (gamma - mk[j]));
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        __half2 h = __floats2half2_rn(mk[2 * j], mk[2 * j + 1]);
+                        mh[j] = *reinterpret_cast<uint32_t*>(&h);
+                    }
+                    ptx::tmem_st16(t_p + ch * 16, pn);
+                    ptx::tmem_st8(t_m + ch * 8, mh);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int c = ch * 16 + j;
+                        if (sF) {
+                            v[j] = mk[j] * sF[c * 128 + lt];
+                        } else {
+                            v[j] = (c < de && mk[j] > 0.f) ? mk[j] * f_value(c, false) : 0.f;
+                        }
+                        if (mrow && c < de) mrow[c] = mk[j];
+                    }
+                    store_a16<SPLIT>(sA, sAlo, lt, ch, v);
+                }
+                ptx::tmem_wait_st();
+            }
+
+            // ---- feature transformer s
+            for (int l = 0; l < lpf; ++l) {
+                const bool first = (l == 0);
+                if (!run_mma(first ? p.k0_blocks : p.kn_blocks, first ? dch : N / 16, idesc_ft)) {
+                    alive = false;
+                    break;
+                }
+                const float* sc = epi + (s * lpf + l) * 4 * N;
+                const float* sh = sc + 2 * N;
+                TC_TRACE(128 + tid / 32, 3000 + lc);
+#pragma unroll
+                for (int cc = 0; cc < RCH; ++cc) {
+                    const int c0 = wg * CPW + cc * 16;
+                    uint32_t lin[16], gat[16];
+                    ptx::tmem_ld16(t_acc + c0, lin);
+                    ptx::tmem_ld16(t_acc + N + c0, gat);
+                    ptx::tmem_wait_ld(lin, gat);
+                    float out[16];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 sl = *reinterpret_cast<const float4*>(sc + c0 + 4 * q);
+                        const float4 hl = *reinterpret_cast<const float4*>(sh + c0 + 4 * q);
+                        const float4 sg = *reinterpret_cast<const float4*>(sc + N + c0 + 4 * q);
+                        const float4 hg = *reinterpret_cast<const float4*>(sh + N + c0 + 4 * q);
+                        const float slv[4] = {sl.x, sl.y, sl.z, sl.w}, hlv[4] = {hl.x, hl.y, hl.z, hl.w};
+                        const float sgv[4] = {sg.x, sg.y, sg.z, sg.w}, hgv[4] = {hg.x, hg.y, hg.z, hg.w};
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const int j = 4 * q + t;
+                            const float ul = fmaf(__uint_as_float(lin[j]), slv[t], hlv[t]);
+                            const float ug = fmaf(__uint_as_float(gat[j]), sgv[t], hgv[t]);
+                            const float g = ul * (SPLIT ? sigmoid_accurate(ug) : sigmoid_fast(ug));
+                            const float x = first ? g : (res[cc][j] + g) * kSqrtHalf;
+                            res[cc][j] = x;
+                            out[j] = x;
+                        }
+                    }
+                    store_a16<SPLIT>(sA, sAlo, lt, c0 / 16, out);
+                }
+            }
+            if (!alive) break;
+
+            if (s > 0) {
+                // ---- decision output: acc += ReLU(d) (folded into the logits), eta, aggregate
+                float eta = 0.f;
+#pragma unroll
+                for (int cc = 0; cc < RCH; ++cc) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int c = wg * CPW + cc * 16 + j;
+                        if (c < n_d) {
+                            const float dv = fmaxf(res[cc][j], 0.f);
+                            eta += dv;
+#pragma unroll
+                            for (int k = 0; k < kMaxClasses; ++k)
+                                if (k < n_cls) lacc[k] = fmaf(sWf[k * n_d + c], dv, lacc[k]);
+                        }
+                    }
+                }
+                eta = xsum(eta, 0.f).x;
+                for (int ch = wg; ch < dch; ch += NWG) {
+                    uint32_t mh[8];
+                    ptx::tmem_ld8(t_m + ch * 8, mh);
+                    ptx::tmem_wait_ld8(mh);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float2 mm = __half22float2(*reinterpret_cast<__half2*>(&mh[j]));
+                        const float mv[2] = {mm.x, mm.y};
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {
+                            const int c = ch * 16 + 2 * j + t;
+                            if (c < de && mv[t] > 0.f) {
+                                float* dst = sAgg + __ldg(p.col_feat + c) * 128 + lt;
+                                if constexpr (NWG == 1) *dst = fmaf(eta, mv[t], *dst);
+                                else atomicAdd(dst, eta * mv[t]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (!alive) break;
+
+        // ---- logits and the normalised aggregate
+#pragma unroll
+        for (int k = 0; k < kMaxClasses; ++k) {
+            if (k < n_cls) {
+                const float v = xsum(lacc[k], 0.f).x;
+                if (wg == 0 && valid) logits[(size_t)row * n_cls + k] = v + __ldg(m.bf + k);
+            }
+        }
+        if constexpr (NWG > 1) ptx::named_bar_sync(2, THREADS);  // every aggregate update is in shared memory
+        float tot = 0.f;
+        for (int j = wg; j < m.d; j += NWG) tot += sAgg[j * 128 + lt];
+        tot = xsum(tot, 0.f).x;
+        if (agg_out && valid) {
+            const float inv = tot > 0.f ? 1.f / tot : 0.f;
+            for (int j = wg; j < m.d; j += NWG)
+                agg_out[(size_t)row * m.d + j] = tot > 0.f ? sAgg[j * 128 + lt] * inv : 0.f;
+        }
+    }
+
+    // ---- teardown: no copy or MMA may still target this CTA's memory
+    TC_TRACE(96 + tid / 32, 900000 + lc);
+    __syncthreads();
+    if (tid == 0) {
+        for (int64_t g = g_cons; g < g_issue; ++g)
+            if (!ptx::mbar_wait(bar_full + 8 * (int)(g % S), (uint32_t)((g / S) & 1), kWaitLimit))
+                note_timeout(m.status, 3, (unsigned)g);
+        if (acc_outstanding && !ptx::mbar_wait(bar_acc, acc_phase ^ 1, kWaitLimit))
+            note_timeout(m.status, 4, (unsigned)lc);
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == 0) ptx::tmem_dealloc(tmem, (uint32_t)p.tmem_cols);
+    TC_TRACE(96 + tid / 32, 999999);
+}
+
+// ---------------------------------------------------------------- host side
+
+uint16_t f32_to_bf16_rne(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)((u >> 16) | ((u & 0xffffu) ? 0x40u : 0u));
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_to_f32(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Pack W [n_out, k_valid] (row-major; input column j lands at K index
+// j + col_shift) into ceil(k_pad / 64) blocks of n_out x 64 bf16 in the
+// 128B-swizzled K-major layout.  part 0: bf16(w); part 1: bf16(w - bf16(w)).
+void pack_sw128(const float* W, int n_out, int k_valid, int col_shift, int k_pad, int part,
+                std::vector<uint8_t>& out) {
+    const int n_blocks = (k_pad + 63) / 64;
+    out.assign((size_t)n_blocks * n_out * 128, 0);
+    for (int b = 0; b < n_blocks; ++b) {
+        uint8_t* blk = out.data() + (size_t)b * n_out * 128;
+        for (int n = 0; n < n_out; ++n) {
+            for (int kk = 0; kk < 64; ++kk) {
+                const int k = b * 64 + kk;
+                const int src = k - col_shift;
+                const float w = (src >= 0 && src < k_valid) ? W[(size_t)n * k_valid + src] : 0.f;
+                const uint16_t hi = f32_to_bf16_rne(w);
+                const uint16_t h = part == 0 ? hi : f32_to_bf16_rne(w - bf16_to_f32(hi));
+                const size_t off = (size_t)(n >> 3) * 1024 + (n & 7) * 128 + ((((kk >> 3) ^ (n & 7)) & 7) << 4) +
+                                   (kk & 7) * 2;
+                std::memcpy(blk + off, &h, 2);
+            }
+        }
+    }
+}
+
+int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+struct Variant {
+    int N, nwg;
+    bool split, zreg;
+};
+
+// Run f on the kernel instantiation of a variant; false when none exists.
+template <typename F>
+bool with_kernel(const Variant& v, F&& f) {
+#define TC_VARIANT(NN, WW)                                                  \
+    if (v.N == NN && v.nwg == WW) {                                         \
+        if (v.split) {                                                      \
+            if (v.zreg) f(tc_forward_kernel<NN, WW, true, true>);            \
+            else f(tc_forward_kernel<NN, WW, true, false>);                  \
+        } else {                                                            \
+            if (v.zreg) f(tc_forward_kernel<NN, WW, false, true>);           \
+            else f(tc_forward_kernel<NN, WW, false, false>);                 \
+        }                                                                   \
+        return true;                                                        \
+    }
+    TC_VARIANT(16, 1)
+    TC_VARIANT(32, 1)
+    TC_VARIANT(32, 2)
+    TC_VARIANT(64, 1)
+    TC_VARIANT(64, 2)
+    TC_VARIANT(128, 2)
+#undef TC_VARIANT
+    return false;
+}
+
+TcSmem smem_layout(int N, int dp, int d, int n_cls, int n_d, int n_slots, int slot_bytes, bool split, int nwg,
+                   int epi_floats, bool with_epi, bool with_f) {
+    TcSmem s{};
+    const int a_blocks = (std::max(dp, N) + 63) / 64;
+    int o = 0;
+    s.a_hi = o; o += a_blocks * 16384;
+    s.a_lo = -1;
+    if (split) { s.a_lo = o; o += a_blocks * 16384; }
+    s.ring = o; o += n_slots * slot_bytes;
+    s.agg = o; o += round_up(d * 128 * 4, 16);
+    s.xch = -1;
+    if (nwg > 1) { s.xch = o; o += 2 * 2 * 128 * 8; }
+    s.wf = o; o += round_up(n_cls * n_d * 4, 16);
+    s.epi = -1;
+    if (with_epi) { s.epi = o; o += round_up(epi_floats * 4, 16); }
+    s.fcache = -1;
+    if (with_f) { s.fcache = o; o += dp * 128 * 4; }
+    s.bar = o; o += round_up((2 * n_slots + 3) * 8, 16);
+    s.total = o;
+    return s;
+}
+
+}  // namespace
+
+int tc_build(tabnet_model* m, Arena& a, std::string* why) {
+    const tabnet_dims& d = m->host.dims;
+    const int N = d.n_d + d.n_a;
+    const int dp = round_up(d.d_emb, 16);
+    const bool split = (m->precision == TABNET_BF16X3);
+    if (m->precision != TABNET_BF16 && m->precision != TABNET_BF16X3) {
+        *why = "fp8 tensor-core path not built";
+        return TABNET_ERR_UNSUPPORTED_DIMS;
+    }
+    if (N != 16 && N != 32 && N != 64 && N != 128) {
+        *why = "tensor-core path needs n_d + n_a in {16, 32, 64, 128}";
+        return TABNET_ERR_UNSUPPORTED_DIMS;
+    }
+    if (dp > 256) { *why = "tensor-core path needs d_emb <= 256"; return TABNET_ERR_UNSUPPORTED_DIMS; }
+    if (d.n_classes > kMaxClasses) { *why = "tensor-core path needs n_classes <= 8"; return TABNET_ERR_UNSUPPORTED_DIMS; }
+    const int accw = std::max(2 * N, dp);
+    const int need = accw + dp + dp / 2;
+    int cols = 32;
+    while (cols < need) cols *= 2;
+    if (cols > 512) { *why = "TMEM budget exceeded"; return TABNET_ERR_UNSUPPORTED_DIMS; }
+    TcParams& p = m->tc;
+    p.dp = dp;
+    p.tmem_cols = cols;
+    p.tm_p = accw;
+    p.tm_m = accw + dp;
+    p.k0_blocks = (dp + 63) / 64;
+    p.kn_blocks = (N + 63) / 64;
+
+    const HostModel& hm = m->host;
+    const int parts = split ? 2 : 1;
+    // Every 64-wide K block of W (hi, then lo in split mode) becomes a chunk.
+    auto push_layer = [&](const float* W, int n_out, int k_valid, int col_shift, int k_pad,
+                          std::vector<std::pair<size_t, uint32_t>>* keep) {
+        const uint32_t cb = (uint32_t)n_out * 128;
+        std::vector<std::vector<uint8_t>> pk(parts);
+        for (int part = 0; part < parts; ++part) pack_sw128(W, n_out, k_valid, col_shift, k_pad, part, pk[part]);
+        const int blocks = (k_pad + 63) / 64;
+        for (int b = 0; b < blocks; ++b)
+            for (int part = 0; part < parts; ++part) {
+                const size_t off = a.add(pk[part].data() + (size_t)b * cb, cb, 1024);
+                keep->push_back({off, cb});
+            }
+    };
+    std::vector<std::vector<std::pair<size_t, uint32_t>>> shared_chunks(d.n_shared);
+    for (int l = 0; l < d.n_shared; ++l)
+        push_layer(hm.shared_fc[l].data(), 2 * N, l == 0 ? d.d_emb : N, 0, l == 0 ? dp : N, &shared_chunks[l]);
+    std::vector<std::pair<size_t, uint32_t>> stream;
+    std::vector<float> epi, att_epi;
+    for (int s = 0; s <= d.n_steps; ++s) {
+        if (s > 0) {
+            // attentive FC [de, n_a] acting on the whole FT output [N] as
+            // [dp, N]: columns [0, n_d) (the decision part) and rows beyond
+            // de (padding) carry zero weight
+            std::vector<float> wp((size_t)dp * d.n_a, 0.f);
+            std::memcpy(wp.data(), hm.att_fc[s - 1].data(), sizeof(float) * d.d_emb * d.n_a);
+            push_layer(wp.data(), dp, d.n_a, d.n_d, N, &stream);
+            std::vector<float> sc, sh;
+            fold_bn(hm.att_bn[s - 1], d.bn_eps, sc, sh);
+            sc.resize(dp, 0.f);
+            sh.resize(dp, 0.f);
+            att_epi.insert(att_epi.end(), sc.begin(), sc.end());
+            att_epi.insert(att_epi.end(), sh.begin(), sh.end());
+        }
+        for (int l = 0; l < d.n_shared + d.n_indep; ++l) {
+            GluLayer g = hm.layer(s, l);
+            if (l < d.n_shared) {
+                stream.insert(stream.end(), shared_chunks[l].begin(), shared_chunks[l].end());
+            } else {
+                push_layer(g.w->data(), 2 * N, g.k, 0, l == 0 ? dp : N, &stream);
+            }
+            std::vector<float> sc, sh;
+            fold_bn(*g.bn, d.bn_eps, sc, sh);
+            epi.insert(epi.end(), sc.begin(), sc.end());
+            epi.insert(epi.end(), sh.begin(), sh.end());
+        }
+    }
+    epi.insert(epi.end(), att_epi.begin(), att_epi.end());
+    m->tc_chunk_off.clear();
+    m->tc_chunk_bytes.clear();
+    for (auto& c : stream) {
+        m->tc_chunk_off.push_back(c.first);
+        m->tc_chunk_bytes.push_back(c.second);
+    }
+    p.chunks_per_tile = (int)stream.size();
+    p.epi_floats = (int)epi.size();
+    m->tc_off_epi = a.add(epi.data(), epi.size() * 4, 16);
+    m->tc_off_chunks = a.add(nullptr, sizeof(uint2) * stream.size(), 16);
+    std::vector<int2> ci(dp);
+    std::vector<int> cf(dp, -1);
+    for (int c = 0; c < dp; ++c) ci[c] = make_int2(-2, 0);
+    for (int c = 0; c < d.n_num; ++c) { ci[c] = make_int2(-1, c); cf[c] = c; }
+    int col = d.n_num;
+    for (int j = 0; j < d.n_cat; ++j)
+        for (int e = 0; e < hm.cat_emb_dim[j]; ++e, ++col) { ci[col] = make_int2(j, e); cf[col] = d.n_num + j; }
+    m->tc_off_colinfo = a.add(ci.data(), sizeof(int2) * dp, 16);
+    m->tc_off_colfeat = a.add(cf.data(), sizeof(int) * dp, 16);
+    return TABNET_OK;
+}
+
+// Pick warpgroups, ring depth, CTAs per SM and what to stage in shared memory.
+int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std::string* why) {
+    const tabnet_dims& d = m->host.dims;
+    const int N = d.n_d + d.n_a;
+    TcParams& p = m->tc;
+    const bool split = (m->precision == TABNET_BF16X3);
+    if (nwg <= 0) nwg = (N == 128) ? 2 : 1;
+    if (N == 128 && nwg != 2) { *why = "N = 128 needs two warpgroups"; return TABNET_ERR_UNSUPPORTED_DIMS; }
+    if (N == 16 && nwg != 1) { *why = "N = 16 takes one warpgroup"; return TABNET_ERR_UNSUPPORTED_DIMS; }
+    if (nwg != 1 && nwg != 2) { *why = "one or two warpgroups"; return TABNET_ERR_UNSUPPORTED_DIMS; }
+    const int dch = p.dp / 16;
+    const bool zreg = (dch + nwg - 1) / nwg <= kZregChunks;
+    const Variant v{N, nwg, split, zreg};
+    cudaFuncAttributes fa{};
+    if (!with_kernel(v, [&](auto fn) { cudaFuncGetAttributes(&fa, fn); })) {
+        *why = "no kernel for this shape";
+        return TABNET_ERR_UNSUPPORTED_DIMS;
+    }
+    const int regs = std::max(fa.numRegs, 1);
+    int dev_smem_sm = 0;
+    cudaDeviceGetAttribute(&dev_smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, m->device);
+    const int reserved = 1024;
+    const int threads = 128 * nwg;
+    const int reg_limit = 65536 / (((regs * 32 + 255) / 256 * 256) * (threads / 32));
+    const int tmem_limit = 512 / p.tmem_cols;
+    const int slot_bytes = std::max(2 * N, p.dp) * 128;
+    const int min_slots = split ? 2 : 1;
+    int cps_max = std::max(1, std::min({tmem_limit, reg_limit, 4}));
+    int best_cps = 0, best_slots = 0;
+    bool best_epi = false, best_f = false;
+    for (int cps = cps_max; cps >= 1 && !best_cps; --cps) {
+        if (ctas_per_sm > 0 && cps != ctas_per_sm) continue;
+        const size_t per_cta = (size_t)dev_smem_sm / cps - reserved;
+        const size_t budget = std::min((size_t)m->smem_optin, per_cta) - 1024;
+        for (int sl = 8; sl >= min_slots; --sl) {
+            if (n_slots > 0 && sl != n_slots) continue;
+            TcSmem s = smem_layout(N, p.dp, d.n_feat, d.n_classes, d.n_d, sl, slot_bytes, split, nwg, p.epi_floats,
+                                   false, false);
+            if ((size_t)s.total > budget) continue;
+            // with several CTAs per SM keep at least two layers' chunks in flight
+            const int want = split ? 4 : 2;
+            if (n_slots <= 0 && ctas_per_sm <= 0 && cps > 1 && sl < want) break;
+            best_cps = cps;
+            best_slots = sl;
+            TcSmem se = smem_layout(N, p.dp, d.n_feat, d.n_classes, d.n_d, sl, slot_bytes, split, nwg,
+                                    p.epi_floats, true, false);
+            best_epi = (size_t)se.total <= budget;
+            TcSmem sf = smem_layout(N, p.dp, d.n_feat, d.n_classes, d.n_d, sl, slot_bytes, split, nwg,
+                                    p.epi_floats, best_epi, true);
+            best_f = (size_t)sf.total <= budget;
+            break;
+        }
+    }
+    if (!best_cps) { *why = "no launch shape fits shared memory"; return TABNET_ERR_UNSUPPORTED_DIMS; }
+    p.n_slots = best_slots;
+    p.slot_bytes = slot_bytes;
+    p.sm = smem_layout(N, p.dp, d.n_feat, d.n_classes, d.n_d, best_slots, slot_bytes, split, nwg, p.epi_floats,
+                       best_epi, best_f);
+    size_t smem = (size_t)p.sm.total + 1024;
+    // request enough shared memory that no more than best_cps CTAs share an SM
+    const size_t floor_smem = (size_t)dev_smem_sm / (best_cps + 1) + 1;
+    if (smem < floor_smem) smem = std::min(floor_smem, (size_t)m->smem_optin);
+    m->tc_launch_cfg.nwg = nwg;
+    m->tc_launch_cfg.n_slots = best_slots;
+    m->tc_launch_cfg.ctas_per_sm = best_cps;
+    m->tc_launch_cfg.smem = smem;
+    m->tc_launch_cfg.zreg = zreg;
+    cudaError_t e = cudaSuccess;
+    with_kernel(v, [&](auto fn) { e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });
+    if (e != cudaSuccess) { *why = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e); return TABNET_ERR_CUDA; }
+    return TABNET_OK;
+}
+
+int tc_patch(tabnet_model* m, Arena& a, const uint8_t* base, std::string* why) {
+    TcParams& p = m->tc;
+    p.m = m->consts;
+    p.wbase = base;
+    std::vector<uint2> ck(m->tc_chunk_off.size());
+    for (size_t i = 0; i < ck.size(); ++i) ck[i] = make_uint2((uint32_t)m->tc_chunk_off[i], m->tc_chunk_bytes[i]);
+    std::memcpy(a.image.data() + m->tc_off_chunks, ck.data(), sizeof(uint2) * ck.size());
+    p.chunks = (const uint2*)(base + m->tc_off_chunks);
+    p.epi = (const float*)(base + m->tc_off_epi);
+    p.col_info = (const int2*)(base + m->tc_off_colinfo);
+    p.col_feat = (const int*)(base + m->tc_off_colfeat);
+    return tc_choose_launch(m, 0, 0, 0, why);
+}
+
+cudaError_t tc_launch(tabnet_model* m, const float* x_num, const int* x_cat, int64_t rows, float* logits,
+                      float* masks, float* agg, cudaStream_t stream) {
+    TcParams p = m->tc;
+    p.num_tiles = (rows + 127) / 128;
+    p.trace = nullptr;
+#ifdef TABNET_TRACE
+    cudaHostGetDevicePointer((void**)&p.trace, tabnet_debug_trace_ptr(), 0);
+#endif
+    const TcLaunch& L = m->tc_launch_cfg;
+    const int64_t slots = (int64_t)m->num_sms * L.ctas_per_sm;
+    const unsigned grid = (unsigned)std::min<int64_t>(p.num_tiles, slots);
+    const dim3 block(128 * L.nwg);
+    const Variant v{p.m.N, L.nwg, m->precision == TABNET_BF16X3, L.zreg};
+    const bool found = with_kernel(v, [&](auto fn) {
+        fn<<<grid, block, L.smem, stream>>>(p, x_num, x_cat, rows, logits, masks, agg);
+    });
+    if (!found) return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+void tc_release(tabnet_model*) {}
+
+#ifdef TABNET_TRACE
+static unsigned* g_trace_host = nullptr;
+unsigned* tabnet_debug_trace_ptr() {
+    if (!g_trace_host) {
+        cudaHostAlloc((void**)&g_trace_host, 4096 * sizeof(unsigned), cudaHostAllocMapped);
+        std::memset(g_trace_host, 0, 4096 * sizeof(unsigned));
+    }
+    return g_trace_host;
+}
+extern "C" unsigned* tabnet_debug_trace(void) { return tabnet_debug_trace_ptr(); }
+#endif
+
+}  // namespace tabnet

@@ -1,0 +1,50 @@
+// Parameter block of the tensor-core (tcgen05) forward kernel.
+#pragma once
+
+#include <cstdint>
+
+#include "kernel_params.h"
+
+namespace tabnet {
+
+// Shared-memory layout of one CTA, byte offsets from a 1024-aligned base;
+// an offset of -1 means the part is not staged (read from global instead).
+struct TcSmem {
+    int a_hi;   // A operand (activations, bf16, SW128 K-major, 16 KB per 64 K-columns)
+    int a_lo;   // low halves of the split-bf16 A operand (-1 unless split)
+    int ring;   // weight-staging ring: n_slots x slot_bytes
+    int agg;    // aggregate per original feature, float [d][128]
+    int xch;    // cross-warpgroup exchange, float2 [2][2][128] (-1 with one warpgroup)
+    int wf;     // final linear weights, float [n_classes][n_d]
+    int epi;    // every layer's folded BN scale/shift (-1: read from global)
+    int fcache; // embedded, BN'd input of the tile, float [dp][128] (-1: recomputed)
+    int bar;    // mbarriers: n_slots full, n_slots empty, 1 accumulator; TMEM address; abort flag
+    int total;  // bytes used (without the alignment slack)
+};
+
+struct TcParams {
+    ModelConsts m;
+    const uint8_t* wbase;      // packed weight chunks (device)
+    const uint2* chunks;       // [chunks_per_tile] {byte offset from wbase, bytes}, stream order
+    int chunks_per_tile;
+    // Every layer's folded BN as one float block: feature-transformer layer
+    // L = s * layers_per_ft + l at L * 4N (scale[2N], shift[2N]), then the
+    // attentive layer of step i at n_ft_layers * 4N + i * 2 dp (scale[dp], shift[dp]).
+    const float* epi;
+    int epi_floats;
+    const int2* col_info;      // [dp]: {-1, numeric column} | {categorical j, element e} | {-2, 0} pad
+    const int* col_feat;       // [dp]: original feature of each embedded column (-1 for pad)
+    int dp;                    // mask width padded to a multiple of 16
+    int k0_blocks;             // 64-wide K blocks of a feature transformer's first layer (K = dp)
+    int kn_blocks;             // 64-wide K blocks of the other layers and of the attentive layer (K = N)
+    int tmem_cols;             // TMEM columns allocated per CTA
+    int tm_p;                  // TMEM column of the prior P (fp32, dp columns)
+    int tm_m;                  // TMEM column of the current mask (fp16 pairs, dp/2 columns)
+    int n_slots;
+    int slot_bytes;
+    TcSmem sm;
+    int64_t num_tiles;
+    unsigned* trace;           // debug builds only (TABNET_TRACE): progress words, else null
+};
+
+}  // namespace tabnet

@@ -1,0 +1,191 @@
+"""ctypes binding of libtabnet.so (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; this module only
+passes pointers, sizes and streams.  PyTorch tensors are accepted for device
+buffers (their data_ptr is passed) and numpy arrays for host buffers.  When
+the shared library is missing the import of any entry point raises: there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtabnet.so")
+
+TABNET_FP32, TABNET_BF16, TABNET_FP8_E4M3, TABNET_BF16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp32": TABNET_FP32, "bf16": TABNET_BF16, "fp8": TABNET_FP8_E4M3, "bf16x3": TABNET_BF16X3}
+
+OK = 0
+ERR = {
+    -1: "ARG", -2: "BLOB_MAGIC", -3: "BLOB_VERSION", -4: "BLOB_SIZE", -5: "BLOB_HASH",
+    -6: "UNSUPPORTED_DIMS", -7: "CUDA", -8: "OOM", -9: "TIMEOUT", -10: "DEVICE",
+}
+STATUS_CAT_OOB = 0x1
+STATUS_TIMEOUT = 0x2
+
+#: every symbol declared in include/tabnet.h
+EXPORTS = (
+    "tabnet_abi_version", "tabnet_blob_inspect", "tabnet_create", "tabnet_dims_of",
+    "tabnet_precision_of", "tabnet_forward", "tabnet_forward_host", "tabnet_poll_status",
+    "tabnet_destroy", "tabnet_status_string", "tabnet_last_error",
+)
+
+
+class TabnetError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {ERR.get(code, code)} ({detail})")
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [
+        ("n_num", ctypes.c_int32), ("n_cat", ctypes.c_int32), ("d_emb", ctypes.c_int32),
+        ("n_feat", ctypes.c_int32), ("n_d", ctypes.c_int32), ("n_a", ctypes.c_int32),
+        ("n_steps", ctypes.c_int32), ("n_shared", ctypes.c_int32), ("n_indep", ctypes.c_int32),
+        ("n_classes", ctypes.c_int32), ("gamma", ctypes.c_double), ("bn_eps", ctypes.c_double),
+        ("content_hash", ctypes.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libtabnet.so (built in-tree by paper_2510_19689_b300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2510_19689_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    L.tabnet_abi_version.restype = i32
+    L.tabnet_blob_inspect.argtypes = [vp, sz, ctypes.POINTER(Dims)]
+    L.tabnet_create.argtypes = [vp, sz, i32, i32, ctypes.POINTER(vp)]
+    L.tabnet_dims_of.argtypes = [vp, ctypes.POINTER(Dims)]
+    L.tabnet_precision_of.argtypes = [vp]
+    L.tabnet_forward.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
+    L.tabnet_forward_host.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
+    L.tabnet_poll_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32)]
+    L.tabnet_destroy.argtypes = [vp]
+    L.tabnet_destroy.restype = None
+    L.tabnet_status_string.argtypes = [i32]
+    L.tabnet_status_string.restype = ctypes.c_char_p
+    L.tabnet_last_error.restype = ctypes.c_char_p
+    for name in ("tabnet_blob_inspect", "tabnet_create", "tabnet_dims_of", "tabnet_precision_of",
+                 "tabnet_forward", "tabnet_forward_host", "tabnet_poll_status"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return lib().tabnet_last_error().decode()
+
+
+def _check(code: int, where: str):
+    if code != OK:
+        raise TabnetError(code, where, last_error())
+
+
+def blob_inspect(blob: bytes) -> Dims:
+    d = Dims()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(lib().tabnet_blob_inspect(buf, len(blob), ctypes.byref(d)), "tabnet_blob_inspect")
+    return d
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Model:
+    """A model loaded on one device at one precision (tabnet_create)."""
+
+    def __init__(self, blob: bytes, precision="bf16", device: int = 0):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().tabnet_create(buf, len(blob), prec, device, ctypes.byref(h)), "tabnet_create")
+        self._h = h
+        self.device = device
+        self.precision = prec
+        d = Dims()
+        _check(lib().tabnet_dims_of(h, ctypes.byref(d)), "tabnet_dims_of")
+        self.dims = d
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def forward(self, x_num, x_cat, rows: int, logits, masks=None, agg=None, stream=None) -> None:
+        """Device buffers (torch tensors or raw pointers); stream-ordered."""
+        _check(lib().tabnet_forward(self._h, _ptr(x_num), _ptr(x_cat), int(rows), _ptr(logits),
+                                    _ptr(masks), _ptr(agg), _stream(stream)), "tabnet_forward")
+
+    def forward_host(self, x_num: np.ndarray, x_cat: np.ndarray, masks=True, agg=True, stream=0):
+        """Host numpy buffers in and out (synchronous)."""
+        d = self.dims
+        rows = x_num.shape[0] if d.n_num else x_cat.shape[0]
+        x_num = np.ascontiguousarray(x_num, dtype=np.float32)
+        x_cat = np.ascontiguousarray(x_cat, dtype=np.int32)
+        lg = np.empty((rows, d.n_classes), np.float32)
+        mk = np.empty((rows, d.n_steps, d.d_emb), np.float32) if masks else None
+        ag = np.empty((rows, d.n_feat), np.float32) if agg else None
+        _check(lib().tabnet_forward_host(self._h, _ptr(x_num) if d.n_num else None,
+                                         _ptr(x_cat) if d.n_cat else None, rows, _ptr(lg),
+                                         _ptr(mk), _ptr(ag), stream), "tabnet_forward_host")
+        return lg, mk, ag
+
+    def poll_status(self, stream=None) -> int:
+        st = ctypes.c_uint32(0)
+        code = lib().tabnet_poll_status(self._h, _stream(stream), ctypes.byref(st))
+        if code not in (OK, -9, -10):
+            _check(code, "tabnet_poll_status")
+        return st.value
+
+    def run(self, x_num, x_cat, stream=None):
+        """Allocate torch outputs on the model's device and run forward."""
+        import torch
+        d = self.dims
+        rows = x_num.shape[0] if d.n_num else x_cat.shape[0]
+        dev = torch.device("cuda", self.device)
+        lg = torch.empty((rows, d.n_classes), dtype=torch.float32, device=dev)
+        mk = torch.empty((rows, d.n_steps, d.d_emb), dtype=torch.float32, device=dev)
+        ag = torch.empty((rows, d.n_feat), dtype=torch.float32, device=dev)
+        self.forward(x_num if d.n_num else None, x_cat if d.n_cat else None, rows, lg, mk, ag, stream)
+        return lg, mk, ag
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tabnet_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
