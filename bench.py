@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Throughput of batched TabNet inference (logits + per-step masks +
+aggregated mask written to device memory) on B300.
+
+Default workload: the 35-input model (26 numeric: 13 lognormal(0,1), 13
+ordinal 1..5; 9 categorical with cardinalities 2..10), n_d = n_a = 32, 5
+decision steps, 2 classes, 65,536 rows per batch, seeded synthetic data and
+weights, split-bf16 tensor-core precision (the mode that meets the bf16
+tolerances against the FP64 oracle).  One step = one forward over one batch.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own batch on its own GPU (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.  The reference
+arm (--impl reference) times the FP64 CPU oracle on bounded samples of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TabNet rows/s (logits+masks) BF16 vs FP32 at stated tol"
+UNIT = "rows/s"
+L2_BYTES = 126 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16", "fp32"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the comparison arms")
+    ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shape")
+    return ap.parse_args()
+
+
+def describe(name):
+    from paper_2510_19689_b300 import synth
+    s = synth.SPECS[name]
+    return (f"{name}: {synth.ROWS[name]:,} rows x {s.n_feat} inputs ({s.n_num} numeric, {s.n_cat} categorical, "
+            f"embedding dim {s.cat_emb_dim[0]}), n_d=n_a={s.n_d}, {s.n_steps} steps, {s.n_classes} classes")
+
+
+def mac_per_row(params):
+    """Algorithmic multiply-adds of one row: every FC at its true width."""
+    N = params["n_d"] + params["n_a"]
+    de = params["n_num"] + sum(params["cat_emb_dim"])
+    lpf = params["n_shared"] + params["n_indep"]
+    ft = de * 2 * N + (lpf - 1) * N * 2 * N
+    return ((params["n_steps"] + 1) * ft + params["n_steps"] * params["n_a"] * de
+            + params["n_d"] * params["n_classes"])
+
+
+def bytes_per_row(params):
+    de = params["n_num"] + sum(params["cat_emb_dim"])
+    d = params["n_num"] + len(params["cat_card"])
+    inp = 4 * params["n_num"] + 4 * len(params["cat_card"])
+    out = 4 * params["n_classes"] + 4 * params["n_steps"] * de + 4 * d
+    return inp, out
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            j = json.load(f)
+        return dict(hbm=j["hbm_gbs"], bf16=j["bf16_tflops"], bf16_sus=j["bf16_tflops_sustained"], src="measured")
+    return dict(hbm=6400.0, bf16=1800.0, bf16_sus=1400.0, src="fallback")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2510_19689_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.startswith("tc_"):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload, precision):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"tc_forward_{workload}_{precision}.md")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("- ") and "=" in line:
+                k, v = line[2:].split("=", 1)
+                kv[k.strip()] = v.strip().strip("`")
+    if kv.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_rows_per_s(params, x_num, x_cat):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample."""
+    from oracle import tabnet_oracle as O
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    t0 = time.perf_counter()
+    O.forward(params, x_num, x_cat)
+    dt = time.perf_counter() - t0
+    return x_num.shape[0] / dt, cores, dt
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2510_19689_b300 import synth
+    name = args.workload
+    params = synth.make_params(synth.SPECS[name], synth.weight_seed(name))
+    sample_rows = {"c1": 1024, "c2": 2048, "c3": 256}[name]
+    x_num, x_cat = synth.make_rows(name, sample_rows)
+    for _ in range(max(0, args.warmup)):
+        oracle_rows_per_s(params, x_num, x_cat)
+    ts = []
+    cores = None
+    for _ in range(args.steps):
+        r, cores, dt = oracle_rows_per_s(params, x_num, x_cat)
+        ts.append(dt)
+    ms = 1e3 * sum(ts) / len(ts)
+    value = sample_rows / (ms / 1e3)
+    sample = f"{sample_rows} rows of the {name} workload per step (float64 numpy oracle)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": describe(name), "sample_rows": sample_rows},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    from paper_2510_19689_b300 import autotune, synth, tabnet
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    name = args.workload
+    params, blob, x_num_h, x_cat_h = synth.load_config(name)
+    rows = x_num_h.shape[0]
+    model = tabnet.Model(blob, args.precision, device=local)
+    d = model.dims
+    inp_b, out_b = bytes_per_row(params)
+    set_bytes = rows * (inp_b + out_b)
+    n_sets = max(2, math.ceil(2 * L2_BYTES / set_bytes))
+    sets = []
+    for _ in range(n_sets):
+        sets.append(dict(
+            xn=torch.from_numpy(x_num_h).to(dev), xc=torch.from_numpy(x_cat_h).to(dev),
+            lg=torch.empty((rows, d.n_classes), device=dev),
+            mk=torch.empty((rows, d.n_steps, d.d_emb), device=dev),
+            ag=torch.empty((rows, d.n_feat), device=dev)))
+    stream = torch.cuda.current_stream(dev)
+
+    def step(k):
+        s = sets[k % n_sets]
+        model.forward(s["xn"], s["xc"], rows, s["lg"], s["mk"], s["ag"], stream=stream)
+
+    tile = None
+    if args.precision != "fp32":
+        s0 = sets[0]
+        if not args.no_tune:
+            autotune.tune(model, s0["xn"], s0["xc"], rows, s0["lg"], s0["mk"], s0["ag"], stream=stream,
+                          cache_path=None)
+        tile = model.tile_config()
+
+    # parity on a sample against the FP64 oracle (bench inputs, bench launch shape)
+    step(0)
+    torch.cuda.synchronize()
+    status = model.poll_status()
+    from oracle import tabnet_oracle as O
+    idx = np.linspace(0, rows - 1, 256).astype(np.int64)
+    rl, rm, ra = O.forward(params, x_num_h[idx], x_cat_h[idx])
+    it = torch.from_numpy(idx).to(dev)
+    lg = sets[0]["lg"][it].cpu().numpy()
+    mk = sets[0]["mk"][it].cpu().numpy()
+    ag = sets[0]["ag"][it].cpu().numpy()
+    parity = {"sample_rows": len(idx), "logit_abs_max": float(np.abs(lg - rl).max()),
+              "mask_l1_max": float(np.abs(mk - rm).sum((1, 2)).max()),
+              "agg_l1_max": float(np.abs(ag - ra).sum(1).max()),
+              "argmax_agreement": float((lg.argmax(1) == rl.argmax(1)).mean()), "status": status}
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(args.steps):
+            step(k)
+        e1.record(stream)
+        e1.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * rows * args.steps / (ms_total / 1e3)
+    clocks = clk.summary()
+
+    extras = {}
+    if rank == 0:
+        # end to end through the host-buffer entry point (pinned host memory)
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+        xn_p, xc_p = pin(x_num_h), pin(x_cat_h)
+        lg_p = torch.empty((rows, d.n_classes)).pin_memory().numpy()
+        mk_p = torch.empty((rows, d.n_steps, d.d_emb)).pin_memory().numpy()
+        ag_p = torch.empty((rows, d.n_feat)).pin_memory().numpy()
+        host_args = [tabnet._ptr(xn_p), tabnet._ptr(xc_p), rows, tabnet._ptr(lg_p), tabnet._ptr(mk_p),
+                     tabnet._ptr(ag_p), stream.cuda_stream]
+        L = tabnet.lib()
+        for _ in range(3):
+            tabnet._check(L.tabnet_forward_host(model._h, *host_args), "tabnet_forward_host")
+        e2e_steps = 20
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            tabnet._check(L.tabnet_forward_host(model._h, *host_args), "tabnet_forward_host")
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        extras["e2e"] = {"value": rows / e2e_s, "unit": UNIT, "h2d_bytes_per_step": rows * inp_b,
+                         "d2h_bytes_per_step": rows * out_b}
+
+    pk = peaks()
+    flop_launch = 2.0 * mac_per_row(params) * rows
+    achieved = flop_launch / (ms_step / 1e3) / 1e12
+    sustained = ms_total > 1000.0
+    peak = pk["bf16_sus"] if sustained else pk["bf16"]
+    traffic = profiled_traffic(name, args.precision) if args.precision != "fp32" else None
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_kind": ("bf16 sustained" if sustained else "bf16 burst") + f", of {pk['src']}",
+                "flop_per_launch": flop_launch,
+                "hbm_frac": (rows * (inp_b + out_b)) / (ms_step / 1e3) / 1e9 / pk["hbm"]}
+
+    if rank == 0 and not args.no_extras:
+        # the FP64 oracle on the host cores (bounded sample)
+        n_cpu = {"c1": 1024, "c2": 8192, "c3": 1024}[name]
+        r, cores, dt = oracle_rows_per_s(params, x_num_h[:n_cpu], x_cat_h[:n_cpu])
+        extras["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                  "sample": f"first {n_cpu} rows of the {name} batch, float64 numpy ({dt:.1f} s)"}
+        # plain FP32 unfused GPU forward (PyTorch eager, TF32 off): the 5x target's divisor
+        from paper_2510_19689_b300.unfused import UnfusedTabNet
+        un = UnfusedTabNet(params, dev)
+        s0 = sets[0]
+        for _ in range(3):
+            un.forward(s0["xn"], s0["xc"])
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(10):
+            un.forward(s0["xn"], s0["xc"])
+        a1.record()
+        a1.synchronize()
+        un_ms = a0.elapsed_time(a1) / 10
+        extras["fp32_unfused"] = {"value": rows / (un_ms / 1e3), "unit": UNIT, "ms_per_step": un_ms}
+        extras["speedup_vs_fp32_unfused"] = value / world / extras["fp32_unfused"]["value"]
+        # the other precisions of the fused library on the same batch
+        for prec in ("bf16", "fp32"):
+            if prec == args.precision:
+                continue
+            m2 = tabnet.Model(blob, prec, device=local)
+            if prec != "fp32" and not args.no_tune:
+                autotune.tune(m2, s0["xn"], s0["xc"], rows, s0["lg"], s0["mk"], s0["ag"], stream=stream,
+                              cache_path=None)
+            reps = 20 if prec != "fp32" else 3
+            for _ in range(2):
+                m2.forward(s0["xn"], s0["xc"], rows, s0["lg"], s0["mk"], s0["ag"], stream=stream)
+            b0 = torch.cuda.Event(enable_timing=True)
+            b1 = torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            for k in range(reps):
+                s = sets[k % n_sets]
+                m2.forward(s["xn"], s["xc"], rows, s["lg"], s["mk"], s["ag"], stream=stream)
+            b1.record(stream)
+            b1.synchronize()
+            extras[f"fused_{prec}"] = {"value": rows / (b0.elapsed_time(b1) / reps / 1e3), "unit": UNIT}
+            m2.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if args.precision != "fp32" else "f32", "data": "synthetic",
+            "config": {"workload": describe(name), "rows_per_gpu": rows, "precision": args.precision,
+                       "parallelism": f"replicas x{world} (rows sharded per GPU, no collective)",
+                       "l2": f"{n_sets} rotating input/output sets of {set_bytes / 1e6:.1f} MB "
+                             f"({n_sets * set_bytes / 1e6:.0f} MB > L2)",
+                       "tile": tile},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "roofline": roofline,
+            "parity": parity,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    model.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -148,6 +148,25 @@ int tabnet_forward_host(tabnet_model* model, const float* x_num, const int32_t* 
                         int64_t rows, float* logits, float* step_masks, float* agg_mask,
                         void* stream);
 
+/* Launch shape of the tensor-core kernels (bf16, split-bf16 precisions):
+ *   nwg          epilogue warpgroups per 128-row tile (1 or 2; 2 is required
+ *                when n_d + n_a = 128, 1 when it is 16)
+ *   n_slots      depth of the shared-memory ring that stages weight blocks
+ *                (>= 1, >= 2 for split-bf16)
+ *   ctas_per_sm  tiles resident per SM (bounded by tensor memory, registers
+ *                and shared memory)
+ * Values <= 0 let the library choose.  What does not fit is reported as
+ * UNSUPPORTED_DIMS and leaves the previous shape in place.  Results may
+ * differ between shapes in the last bits (sums split across warpgroups).
+ * Not thread-safe against concurrent forward calls on the same handle.
+ * This is the hook of the autotuner (paper_2510_19689_b300.autotune).
+ * Errors: ARG, UNSUPPORTED_DIMS (also for the fp32 precision), CUDA. */
+int tabnet_set_tile_config(tabnet_model* model, int nwg, int n_slots, int ctas_per_sm);
+
+/* The launch shape in use (each output may be NULL).  Errors: ARG,
+ * UNSUPPORTED_DIMS for the fp32 precision. */
+int tabnet_get_tile_config(const tabnet_model* model, int* nwg, int* n_slots, int* ctas_per_sm);
+
 /* Read and clear the handle's device status word (TABNET_STATUS_* bits) after
  * synchronising `stream`.  *status receives the bits; returns TABNET_OK when
  * no bit was set, TABNET_ERR_TIMEOUT when the timeout bit was set, else

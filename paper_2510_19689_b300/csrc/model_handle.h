@@ -69,5 +69,6 @@ int tc_patch(tabnet_model* m, Arena& a, const uint8_t* base, std::string* why);
 cudaError_t tc_launch(tabnet_model* m, const float* x_num, const int* x_cat, int64_t rows,
                       float* logits, float* masks, float* agg, cudaStream_t stream);
 void tc_release(tabnet_model* m);
+int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std::string* why);
 
 }  // namespace tabnet

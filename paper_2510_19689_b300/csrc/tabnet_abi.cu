@@ -419,6 +419,34 @@ int tabnet_forward_host(tabnet_model* m, const float* x_num, const int32_t* x_ca
     return TABNET_OK;
 }
 
+int tabnet_set_tile_config(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm) {
+    if (!m) return fail(TABNET_ERR_ARG, "null model");
+    if (m->precision != TABNET_BF16 && m->precision != TABNET_BF16X3)
+        return fail(TABNET_ERR_UNSUPPORTED_DIMS, "tile shapes apply to the tensor-core precisions");
+    DeviceGuard guard(m->device);
+    if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+    const TcParams saved_p = m->tc;
+    const TcLaunch saved_l = m->tc_launch_cfg;
+    std::string why;
+    int rc = tc_choose_launch(m, nwg, n_slots, ctas_per_sm, &why);
+    if (rc != TABNET_OK) {
+        m->tc = saved_p;
+        m->tc_launch_cfg = saved_l;
+        return fail(rc, why);
+    }
+    return TABNET_OK;
+}
+
+int tabnet_get_tile_config(const tabnet_model* m, int* nwg, int* n_slots, int* ctas_per_sm) {
+    if (!m) return fail(TABNET_ERR_ARG, "null model");
+    if (m->precision != TABNET_BF16 && m->precision != TABNET_BF16X3)
+        return fail(TABNET_ERR_UNSUPPORTED_DIMS, "tile shapes apply to the tensor-core precisions");
+    if (nwg) *nwg = m->tc_launch_cfg.nwg;
+    if (n_slots) *n_slots = m->tc_launch_cfg.n_slots;
+    if (ctas_per_sm) *ctas_per_sm = m->tc_launch_cfg.ctas_per_sm;
+    return TABNET_OK;
+}
+
 int tabnet_poll_status(tabnet_model* m, void* stream, uint32_t* status) {
     if (!m || !status) return fail(TABNET_ERR_ARG, "null pointer");
     DeviceGuard guard(m->device);

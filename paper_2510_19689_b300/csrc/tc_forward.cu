@@ -128,6 +128,13 @@ __device__ __forceinline__ void store_a16(uint8_t* sA, uint8_t* sAlo, int r, int
     }
 }
 
+// Folded-BN vectors: staged in shared memory (epi_s != 0, a shared address)
+// or read through the read-only path from global memory.
+__device__ __forceinline__ float4 ld_epi(const float* g, uint32_t epi_s, int idx) {
+    if (epi_s) return ptx::ld_shared_f4(epi_s + 4u * (uint32_t)idx);
+    return __ldg(reinterpret_cast<const float4*>(g + idx));
+}
+
 template <int N, int NWG, bool SPLIT, bool ZREG>
 __global__ void __launch_bounds__(128 * NWG, 1)
 tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* __restrict__ x_cat,
@@ -150,8 +157,9 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     float* sAgg = reinterpret_cast<float*>(smem + p.sm.agg);
     float2* sX = reinterpret_cast<float2*>(smem + (p.sm.xch >= 0 ? p.sm.xch : 0));
     float* sWf = reinterpret_cast<float*>(smem + p.sm.wf);
-    float* sF = p.sm.fcache >= 0 ? reinterpret_cast<float*>(smem + p.sm.fcache) : nullptr;
-    const float* epi = p.sm.epi >= 0 ? reinterpret_cast<const float*>(smem + p.sm.epi) : p.epi;
+    const uint32_t f_s = p.sm.fcache >= 0 ? ptx::smem_u32(smem + p.sm.fcache) : 0u;  // f cache (shared address)
+    const uint32_t epi_s = p.sm.epi >= 0 ? ptx::smem_u32(smem + p.sm.epi) : 0u;      // BN vectors (shared address)
+    const float* epi = p.epi;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.sm.bar);
     const int S = p.n_slots;
     volatile uint32_t* sTmem = reinterpret_cast<volatile uint32_t*>(bars + 2 * S + 1);
@@ -324,7 +332,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 v[j] = f_value(ch * 16 + j, valid);
-                if (sF) sF[(ch * 16 + j) * 128 + lt] = v[j];
+                if (f_s) reinterpret_cast<float*>(smem + p.sm.fcache)[(ch * 16 + j) * 128 + lt] = v[j];
             }
             store_a16<SPLIT>(sA, sAlo, lt, ch, v);
             uint32_t ones[16];
@@ -343,8 +351,8 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             if (s > 0) {
                 // ---- attentive transformer of step s: z = (W_att a) * scale + shift, times P
                 if (!run_mma(p.kn_blocks, N / 16, idesc_att)) { alive = false; break; }
-                const float* asc = epi + n_ft_layers * 4 * N + (s - 1) * 2 * p.dp;
-                const float* ash = asc + p.dp;
+                const int asc = n_ft_layers * 4 * N + (s - 1) * 2 * p.dp;  // float index of the scale
+                const int ash = asc + p.dp;
                 auto load_z = [&](int ch, float (&z)[16], uint32_t (&pr)[16]) {
                     uint32_t acc[16];
                     ptx::tmem_ld16(t_acc + ch * 16, acc);
@@ -352,8 +360,8 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     ptx::tmem_wait_ld(acc, pr);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 a = *reinterpret_cast<const float4*>(asc + ch * 16 + 4 * q);
-                        const float4 b = *reinterpret_cast<const float4*>(ash + ch * 16 + 4 * q);
+                        const float4 a = ld_epi(epi, epi_s, asc + ch * 16 + 4 * q);
+                        const float4 b = ld_epi(epi, epi_s, ash + ch * 16 + 4 * q);
                         const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
                         for (int t = 0; t < 4; ++t) {
@@ -473,8 +481,8 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int c = ch * 16 + j;
-                        if (sF) {
-                            v[j] = mk[j] * sF[c * 128 + lt];
+                        if (f_s) {
+                            v[j] = mk[j] * ptx::ld_shared_f32(f_s + 4u * (uint32_t)(c * 128 + lt));
                         } else {
                             v[j] = (c < de && mk[j] > 0.f) ? mk[j] * f_value(c, false) : 0.f;
                         }
@@ -492,8 +500,8 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     alive = false;
                     break;
                 }
-                const float* sc = epi + (s * lpf + l) * 4 * N;
-                const float* sh = sc + 2 * N;
+                const int sc = (s * lpf + l) * 4 * N;  // float index of the layer's scale
+                const int sh = sc + 2 * N;
                 TC_TRACE(128 + tid / 32, 3000 + lc);
 #pragma unroll
                 for (int cc = 0; cc < RCH; ++cc) {
@@ -505,10 +513,10 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     float out[16];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 sl = *reinterpret_cast<const float4*>(sc + c0 + 4 * q);
-                        const float4 hl = *reinterpret_cast<const float4*>(sh + c0 + 4 * q);
-                        const float4 sg = *reinterpret_cast<const float4*>(sc + N + c0 + 4 * q);
-                        const float4 hg = *reinterpret_cast<const float4*>(sh + N + c0 + 4 * q);
+                        const float4 sl = ld_epi(epi, epi_s, sc + c0 + 4 * q);
+                        const float4 hl = ld_epi(epi, epi_s, sh + c0 + 4 * q);
+                        const float4 sg = ld_epi(epi, epi_s, sc + N + c0 + 4 * q);
+                        const float4 hg = ld_epi(epi, epi_s, sh + N + c0 + 4 * q);
                         const float slv[4] = {sl.x, sl.y, sl.z, sl.w}, hlv[4] = {hl.x, hl.y, hl.z, hl.w};
                         const float sgv[4] = {sg.x, sg.y, sg.z, sg.w}, hgv[4] = {hg.x, hg.y, hg.z, hg.w};
 #pragma unroll

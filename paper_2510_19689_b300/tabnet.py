@@ -32,7 +32,8 @@ STATUS_TIMEOUT = 0x2
 EXPORTS = (
     "tabnet_abi_version", "tabnet_blob_inspect", "tabnet_create", "tabnet_dims_of",
     "tabnet_precision_of", "tabnet_forward", "tabnet_forward_host", "tabnet_poll_status",
-    "tabnet_destroy", "tabnet_status_string", "tabnet_last_error",
+    "tabnet_destroy", "tabnet_status_string", "tabnet_last_error", "tabnet_set_tile_config",
+    "tabnet_get_tile_config",
 )
 
 
@@ -75,13 +76,17 @@ def lib() -> ctypes.CDLL:
     L.tabnet_forward.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
     L.tabnet_forward_host.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
     L.tabnet_poll_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32)]
+    L.tabnet_set_tile_config.argtypes = [vp, i32, i32, i32]
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.tabnet_get_tile_config.argtypes = [vp, ip, ip, ip]
     L.tabnet_destroy.argtypes = [vp]
     L.tabnet_destroy.restype = None
     L.tabnet_status_string.argtypes = [i32]
     L.tabnet_status_string.restype = ctypes.c_char_p
     L.tabnet_last_error.restype = ctypes.c_char_p
     for name in ("tabnet_blob_inspect", "tabnet_create", "tabnet_dims_of", "tabnet_precision_of",
-                 "tabnet_forward", "tabnet_forward_host", "tabnet_poll_status"):
+                 "tabnet_forward", "tabnet_forward_host", "tabnet_poll_status",
+                 "tabnet_set_tile_config", "tabnet_get_tile_config"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -159,6 +164,15 @@ class Model:
                                          _ptr(x_cat) if d.n_cat else None, rows, _ptr(lg),
                                          _ptr(mk), _ptr(ag), stream), "tabnet_forward_host")
         return lg, mk, ag
+
+    def set_tile_config(self, nwg: int = 0, n_slots: int = 0, ctas_per_sm: int = 0) -> None:
+        _check(lib().tabnet_set_tile_config(self._h, nwg, n_slots, ctas_per_sm), "tabnet_set_tile_config")
+
+    def tile_config(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().tabnet_get_tile_config(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "tabnet_get_tile_config")
+        return dict(nwg=a.value, n_slots=b.value, ctas_per_sm=c.value)
 
     def poll_status(self, stream=None) -> int:
         st = ctypes.c_uint32(0)
