@@ -136,6 +136,47 @@ int tabnet_forward(tabnet_model* model, const float* x_num, const int32_t* x_cat
                    int64_t rows, float* logits, float* step_masks, float* agg_mask,
                    void* stream);
 
+/* One request of a segmented launch: its own device buffers, laid out as in
+ * tabnet_forward (rows may be 0; step_masks / agg_mask may be NULL). */
+typedef struct {
+    const float* x_num;     /* device [rows, n_num] */
+    const int32_t* x_cat;   /* device [rows, n_cat] */
+    int64_t rows;
+    float* logits;          /* device [rows, n_classes] */
+    float* step_masks;      /* device [rows, n_steps, d_emb] or NULL */
+    float* agg_mask;        /* device [rows, n_feat] or NULL */
+} tabnet_segment;
+
+/* Many independent request batches of uneven size in ONE persistent kernel
+ * launch (the paper's per-invocation batch size, Sec. III-B, served for many
+ * invocations at once).  The rows of all segments are packed back to back
+ * into 128-row tiles (a tile may span segments, so small requests waste no
+ * tile); every row reads and writes its own segment's buffers.
+ *   segs   HOST array of n_segs descriptors (copied before return; the call
+ *          may wait for the previous call's copy of the same handle)
+ * The device side needs (n_segs + 1) 8-byte prefix sums of scratch, owned by
+ * the handle and grown on demand.  Not for stream capture (it stages through
+ * host memory): use tabnet_forward_segments_device for CUDA graphs.
+ * Errors: ARG (null, n_segs < 0, a segment with rows < 0 or a NULL required
+ * pointer), OOM, CUDA. */
+int tabnet_forward_segments(tabnet_model* model, const tabnet_segment* segs, int n_segs, void* stream);
+
+/* As tabnet_forward_segments with the descriptors already in DEVICE memory
+ * (caller-owned, read by the kernels on `stream`, never written).  A scan
+ * kernel computes the prefix sums on the device, so the call makes no host
+ * round trip and can be captured in a CUDA graph, provided the scratch was
+ * reserved beforehand (tabnet_reserve_segments) for at least n_segs; a
+ * capture that would need more scratch fails with OOM instead of allocating.
+ * Segment rows are not validated on the host (a negative count is treated
+ * as 0 by the scan).  Errors: ARG, OOM, CUDA. */
+int tabnet_forward_segments_device(tabnet_model* model, const tabnet_segment* segs, int n_segs,
+                                   void* stream);
+
+/* Reserve the segmented launches' scratch for up to max_segs segments
+ * (device memory owned by the handle, freed by tabnet_destroy).
+ * Errors: ARG, OOM. */
+int tabnet_reserve_segments(tabnet_model* model, int max_segs);
+
 /* Same computation with HOST buffers (pinned or pageable): the inputs are
  * copied into a device workspace owned by the handle, the forward runs, and
  * the outputs are copied back, all on `stream`; the call returns after the

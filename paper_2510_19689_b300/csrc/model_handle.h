@@ -51,6 +51,7 @@ struct tabnet_model {
     // FP32 path
     tabnet::SimtParams simt{};
     int simt_rows = 0;
+    int simt_max_ctas = 0;
     // tensor-core path
     tabnet::TcParams tc{};
     tabnet::TcLaunch tc_launch_cfg{};
@@ -60,6 +61,12 @@ struct tabnet_model {
     // host-buffer forward workspace
     void* d_ws = nullptr;
     size_t ws_bytes = 0;
+    // segmented launches: device descriptors (host-staged calls) + prefix sums
+    void* d_seg = nullptr;
+    int seg_cap = 0;
+    tabnet_segment* h_seg_stage = nullptr;  // pinned staging for host descriptors
+    int seg_stage_cap = 0;
+    cudaEvent_t seg_stage_done = nullptr;
 };
 
 namespace tabnet {
@@ -67,7 +74,8 @@ namespace tabnet {
 int tc_build(tabnet_model* m, Arena& a, std::string* why);
 int tc_patch(tabnet_model* m, Arena& a, const uint8_t* base, std::string* why);
 cudaError_t tc_launch(tabnet_model* m, const float* x_num, const int* x_cat, int64_t rows,
-                      float* logits, float* masks, float* agg, cudaStream_t stream);
+                      float* logits, float* masks, float* agg, cudaStream_t stream,
+                      const SegTable* seg = nullptr);
 void tc_release(tabnet_model* m);
 int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std::string* why);
 

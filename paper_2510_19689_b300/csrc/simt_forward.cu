@@ -11,6 +11,8 @@
 // four lanes of a row read consecutive outputs.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "../../include/tabnet.h"
 #include "kernel_params.h"
 
@@ -112,19 +114,23 @@ simt_forward_kernel(const SimtParams p, const float* __restrict__ x_num,
     float* ACC = AGG + D * ROWS;      // [n_d]  decision accumulator
 
     const int r = threadIdx.x / TPR, q = threadIdx.x % TPR;
-    const int64_t row = (int64_t)blockIdx.x * ROWS + r;
-    const bool valid = row < rows;
+    const int64_t total = total_rows(p.seg, rows);
+    const int64_t num_tiles = (total + ROWS - 1) / ROWS;
+  for (int64_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+    const RowIO io = row_io(p.seg, m, tile * ROWS + r, total, x_num, x_cat, logits, masks, agg_out);
+    const bool valid = io.valid;
+    __syncwarp(row_mask());
 
     // Embedding lookup and input BN (features j = q mod 4).
     for (int j = q; j < D; j += TPR) {
         const int c0 = m.feat_col[j];
         if (j < m.n_num) {
-            const float x = valid ? x_num[row * m.n_num + j] : 0.f;
+            const float x = valid ? io.x_num[j] : 0.f;
             F[c0 * ROWS + r] = fmaf(__ldg(m.s0 + c0), x, __ldg(m.t0 + c0));
         } else {
             const int jc = j - m.n_num;
             const int len = m.feat_len[j];
-            const int idx = valid ? x_cat[row * m.n_cat + jc] : 0;
+            const int idx = valid ? io.x_cat[jc] : 0;
             const bool oob = idx < 0 || idx >= m.cat_card[jc];
             if (oob) atomicOr(m.status, TABNET_STATUS_CAT_OOB);
             const float* t = m.emb + m.cat_off[jc] + (size_t)(oob ? 0 : idx) * len;
@@ -171,7 +177,7 @@ simt_forward_kernel(const SimtParams p, const float* __restrict__ x_num,
             tau = (ss - 1.f) / (float)cnt;
         }
         // Mask, prior update, masked input, mask output.
-        float* mrow = (masks && valid) ? masks + ((size_t)row * m.n_steps + i) * de : nullptr;
+        float* mrow = (io.masks && valid) ? io.masks + (size_t)i * de : nullptr;
         for (int c = q; c < de; c += TPR) {
             const float mk = fmaxf(Z[c * ROWS + r] - tau, 0.f);
             Z[c * ROWS + r] = mk;
@@ -202,16 +208,16 @@ simt_forward_kernel(const SimtParams p, const float* __restrict__ x_num,
     for (int k = q; k < m.n_classes; k += TPR) {
         float acc = __ldg(m.bf + k);
         for (int c = 0; c < n_d; ++c) acc = fmaf(__ldg(m.wf + (size_t)k * n_d + c), ACC[c * ROWS + r], acc);
-        if (valid) logits[(size_t)row * m.n_classes + k] = acc;
+        if (valid) io.logits[k] = acc;
     }
     float tot = 0.f;
     for (int j = q; j < D; j += TPR) tot += AGG[j * ROWS + r];
     tot = sum4(tot);
-    if (agg_out && valid) {
+    if (io.agg && valid) {
         const float inv = tot > 0.f ? 1.f / tot : 0.f;
-        for (int j = q; j < D; j += TPR)
-            agg_out[(size_t)row * D + j] = tot > 0.f ? AGG[j * ROWS + r] * inv : 0.f;
+        for (int j = q; j < D; j += TPR) io.agg[j] = tot > 0.f ? AGG[j * ROWS + r] * inv : 0.f;
     }
+  }
 }
 
 }  // namespace
@@ -228,6 +234,17 @@ int simt_pick_rows(const ModelConsts& m, size_t smem_limit) {
     return 0;
 }
 
+int simt_occupancy(int rows_per_cta, size_t smem) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (rows_per_cta) {
+        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_forward_kernel<32>, 32 * TPR, smem); break;
+        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_forward_kernel<16>, 16 * TPR, smem); break;
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_forward_kernel<8>, 8 * TPR, smem); break;
+    }
+    return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
 cudaError_t simt_configure(int rows_per_cta, size_t smem) {
     switch (rows_per_cta) {
         case 32: return cudaFuncSetAttribute(simt_forward_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -238,10 +255,13 @@ cudaError_t simt_configure(int rows_per_cta, size_t smem) {
 }
 
 cudaError_t simt_launch(const SimtParams& p, int rows_per_cta, const float* x_num, const int* x_cat,
-                        int64_t rows, float* logits, float* masks, float* agg, cudaStream_t stream) {
+                        int64_t rows, float* logits, float* masks, float* agg, cudaStream_t stream,
+                        int max_ctas) {
     const size_t smem = simt_smem_bytes(p.m, rows_per_cta);
-    const int64_t grid = (rows + rows_per_cta - 1) / rows_per_cta;
-    if (grid > 0x7fffffff) return cudaErrorInvalidValue;
+    // persistent: at most max_ctas CTAs loop over the tiles (a segmented
+    // launch learns its row count on the device and takes all of them)
+    int64_t grid = p.seg.segs ? max_ctas : std::min<int64_t>((rows + rows_per_cta - 1) / rows_per_cta, max_ctas);
+    if (grid < 1) grid = 1;
     const dim3 block(rows_per_cta * TPR);
     switch (rows_per_cta) {
         case 32: simt_forward_kernel<32><<<(unsigned)grid, block, smem, stream>>>(p, x_num, x_cat, rows, logits, masks, agg); break;

@@ -22,7 +22,11 @@ size_t simt_smem_bytes(const ModelConsts& m, int rows_per_cta);
 int simt_pick_rows(const ModelConsts& m, size_t smem_limit);
 cudaError_t simt_configure(int rows_per_cta, size_t smem);
 cudaError_t simt_launch(const SimtParams& p, int rows_per_cta, const float* x_num, const int* x_cat,
-                        int64_t rows, float* logits, float* masks, float* agg, cudaStream_t stream);
+                        int64_t rows, float* logits, float* masks, float* agg, cudaStream_t stream,
+                        int max_ctas);
+int simt_occupancy(int rows_per_cta, size_t smem);
+// segments.cu
+cudaError_t seg_prefix_launch(const tabnet_segment* segs, int n, int64_t* prefix, cudaStream_t stream);
 
 namespace {
 
@@ -205,12 +209,14 @@ int check_ptr(const void* p, bool required, const char* name) {
 }  // namespace
 
 int forward_impl(tabnet_model* m, const float* x_num, const int32_t* x_cat, int64_t rows,
-                 float* logits, float* masks, float* agg, cudaStream_t stream) {
+                 float* logits, float* masks, float* agg, cudaStream_t stream, const SegTable* seg = nullptr) {
     cudaError_t e;
     if (m->precision == TABNET_FP32) {
-        e = simt_launch(m->simt, m->simt_rows, x_num, x_cat, rows, logits, masks, agg, stream);
+        SimtParams p = m->simt;
+        p.seg = seg ? *seg : SegTable{nullptr, nullptr, 0};
+        e = simt_launch(p, m->simt_rows, x_num, x_cat, rows, logits, masks, agg, stream, m->simt_max_ctas);
     } else {
-        e = tc_launch(m, x_num, x_cat, rows, logits, masks, agg, stream);
+        e = tc_launch(m, x_num, x_cat, rows, logits, masks, agg, stream, seg);
     }
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return TABNET_OK;
@@ -324,6 +330,7 @@ int tabnet_create(const void* blob, size_t blob_bytes, int precision, int device
                 tabnet_destroy(m);
                 return cuda_fail(e, "cudaFuncSetAttribute");
             }
+            m->simt_max_ctas = m->num_sms * simt_occupancy(m->simt_rows, simt_smem_bytes(m->consts, m->simt_rows));
         } else {
             rc = tc_patch(m, arena, base, &why);
             if (rc != TABNET_OK) { tabnet_destroy(m); return fail(rc, why); }
@@ -419,6 +426,103 @@ int tabnet_forward_host(tabnet_model* m, const float* x_num, const int32_t* x_ca
     return TABNET_OK;
 }
 
+namespace {
+
+// Scratch of the segmented launches: [descriptors: cap][prefix: cap + 1].
+int seg_reserve(tabnet_model* m, int n, cudaStream_t stream) {
+    if (n <= m->seg_cap) return TABNET_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return fail(TABNET_ERR_OOM, "segment scratch too small during stream capture: reserve it first");
+    int cap = std::max(n, std::max(256, 2 * m->seg_cap));
+    void* p = nullptr;
+    const size_t bytes = (size_t)cap * sizeof(tabnet_segment) + ((size_t)cap + 1) * sizeof(int64_t);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(segment scratch)");
+    if (m->d_seg) {
+        cudaDeviceSynchronize();  // the old scratch may still be read by a launch in flight
+        cudaFree(m->d_seg);
+    }
+    m->d_seg = p;
+    m->seg_cap = cap;
+    return TABNET_OK;
+}
+
+int segments_device(tabnet_model* m, const tabnet_segment* segs, int n, cudaStream_t s) {
+    int rc = seg_reserve(m, n, s);
+    if (rc != TABNET_OK) return rc;
+    int64_t* prefix = reinterpret_cast<int64_t*>(static_cast<uint8_t*>(m->d_seg) +
+                                                 (size_t)m->seg_cap * sizeof(tabnet_segment));
+    cudaError_t e = seg_prefix_launch(segs, n, prefix, s);
+    if (e != cudaSuccess) return cuda_fail(e, "segment prefix launch");
+    const SegTable t{segs, prefix, n};
+    return forward_impl(m, nullptr, nullptr, 0, nullptr, nullptr, nullptr, s, &t);
+}
+
+}  // namespace
+
+int tabnet_reserve_segments(tabnet_model* m, int max_segs) {
+    if (!m || max_segs < 0) return fail(TABNET_ERR_ARG, "null model or negative count");
+    DeviceGuard guard(m->device);
+    if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+    return seg_reserve(m, max_segs, nullptr);
+}
+
+int tabnet_forward_segments_device(tabnet_model* m, const tabnet_segment* segs, int n_segs, void* stream) {
+    if (!m || n_segs < 0) return fail(TABNET_ERR_ARG, "null model or negative count");
+    if (n_segs == 0) return TABNET_OK;
+    if (!segs) return fail(TABNET_ERR_ARG, "segs is NULL");
+    DeviceGuard guard(m->device);
+    if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+    return segments_device(m, segs, n_segs, (cudaStream_t)stream);
+}
+
+int tabnet_forward_segments(tabnet_model* m, const tabnet_segment* segs, int n_segs, void* stream) {
+    if (!m || n_segs < 0) return fail(TABNET_ERR_ARG, "null model or negative count");
+    if (n_segs == 0) return TABNET_OK;
+    if (!segs) return fail(TABNET_ERR_ARG, "segs is NULL");
+    const tabnet_dims& d = m->host.dims;
+    for (int i = 0; i < n_segs; ++i) {
+        const tabnet_segment& g = segs[i];
+        if (g.rows < 0) return fail(TABNET_ERR_ARG, "segment " + std::to_string(i) + " has rows < 0");
+        if (g.rows == 0) continue;
+        int rc;
+        if ((rc = check_ptr(g.x_num, d.n_num > 0, "segment x_num")) || (rc = check_ptr(g.x_cat, d.n_cat > 0, "segment x_cat")) ||
+            (rc = check_ptr(g.logits, true, "segment logits")) || (rc = check_ptr(g.step_masks, false, "segment step_masks")) ||
+            (rc = check_ptr(g.agg_mask, false, "segment agg_mask")))
+            return rc;
+    }
+    DeviceGuard guard(m->device);
+    if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    int rc = seg_reserve(m, n_segs, s);
+    if (rc != TABNET_OK) return rc;
+    if (n_segs > m->seg_stage_cap) {
+        if (m->h_seg_stage) {
+            if (m->seg_stage_done) cudaEventSynchronize(m->seg_stage_done);
+            cudaFreeHost(m->h_seg_stage);
+            m->h_seg_stage = nullptr;
+            m->seg_stage_cap = 0;
+        }
+        if ((e = cudaHostAlloc((void**)&m->h_seg_stage, sizeof(tabnet_segment) * (size_t)m->seg_cap,
+                               cudaHostAllocDefault)) != cudaSuccess)
+            return cuda_fail(e, "cudaHostAlloc(segment staging)");
+        m->seg_stage_cap = m->seg_cap;
+    }
+    if (!m->seg_stage_done && (e = cudaEventCreateWithFlags(&m->seg_stage_done, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventCreate");
+    // the previous call's upload must have left the staging buffer
+    if ((e = cudaEventSynchronize(m->seg_stage_done)) != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    std::memcpy(m->h_seg_stage, segs, sizeof(tabnet_segment) * (size_t)n_segs);
+    tabnet_segment* d_segs = static_cast<tabnet_segment*>(m->d_seg);
+    if ((e = cudaMemcpyAsync(d_segs, m->h_seg_stage, sizeof(tabnet_segment) * (size_t)n_segs,
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "upload segment descriptors");
+    if ((e = cudaEventRecord(m->seg_stage_done, s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    return segments_device(m, d_segs, n_segs, s);
+}
+
 int tabnet_set_tile_config(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm) {
     if (!m) return fail(TABNET_ERR_ARG, "null model");
     if (m->precision != TABNET_BF16 && m->precision != TABNET_BF16X3)
@@ -478,6 +582,9 @@ void tabnet_destroy(tabnet_model* m) {
         if (m->d_arena) cudaFree(m->d_arena);
         if (m->d_status) cudaFree(m->d_status);
         if (m->d_ws) cudaFree(m->d_ws);
+        if (m->d_seg) cudaFree(m->d_seg);
+        if (m->h_seg_stage) cudaFreeHost(m->h_seg_stage);
+        if (m->seg_stage_done) cudaEventDestroy(m->seg_stage_done);
         tc_release(m);
     }
     delete m;

@@ -194,8 +194,10 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     const uint32_t t_p = t_acc + (uint32_t)p.tm_p;
     const uint32_t t_m = t_acc + (uint32_t)p.tm_m;
 
+    const int64_t total = total_rows(p.seg, rows);
+    const int64_t num_tiles = (total + 127) / 128;
     const int64_t my_tiles =
-        (int64_t)blockIdx.x < p.num_tiles ? (p.num_tiles - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
+        (int64_t)blockIdx.x < num_tiles ? (num_tiles - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t total_chunks = my_tiles * p.chunks_per_tile;
     int64_t g_issue = 0, g_cons = 0;   // thread 0 only
     bool acc_outstanding = false;      // thread 0 only
@@ -303,19 +305,19 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     const int n_ft_layers = (m.n_steps + 1) * lpf;
 
     bool alive = true;
-    for (int64_t tile = blockIdx.x; tile < p.num_tiles && alive; tile += gridDim.x) {
-        const int64_t row = tile * 128 + lt;
-        const bool valid = row < rows;
+    for (int64_t tile = blockIdx.x; tile < num_tiles && alive; tile += gridDim.x) {
+        const RowIO io = row_io(p.seg, m, tile * 128 + lt, total, x_num, x_cat, logits, masks, agg_out);
+        const bool valid = io.valid;
 
         // Embedded, BN'd input value of column c for this row.
         auto f_value = [&](int c, bool check) -> float {
             const int2 ci = __ldg(p.col_info + c);
             if (ci.x == -1) {
-                const float x = valid ? __ldg(x_num + row * m.n_num + ci.y) : 0.f;
+                const float x = valid ? __ldg(io.x_num + ci.y) : 0.f;
                 return fmaf(__ldg(m.s0 + c), x, __ldg(m.t0 + c));
             }
             if (ci.x >= 0) {
-                const int idx = valid ? __ldg(x_cat + row * m.n_cat + ci.x) : 0;
+                const int idx = valid ? __ldg(io.x_cat + ci.x) : 0;
                 if (idx < 0 || idx >= __ldg(m.cat_card + ci.x)) {
                     if (check) atomicOr(m.status, TABNET_STATUS_CAT_OOB);
                     return __ldg(m.t0 + c);
@@ -444,7 +446,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 }
                 TC_TRACE(128 + tid / 32, 4000 + lc);
                 // Mask, prior, masked input (A for the step's first FC), outputs.
-                float* mrow = (masks && valid) ? masks + ((size_t)row * m.n_steps + (s - 1)) * de : nullptr;
+                float* mrow = (io.masks && valid) ? io.masks + (size_t)(s - 1) * de : nullptr;
 #pragma unroll 1
                 for (int il = 0; wg + il * NWG < dch; ++il) {
                     const int ch = wg + il * NWG;
@@ -581,17 +583,16 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         for (int k = 0; k < kMaxClasses; ++k) {
             if (k < n_cls) {
                 const float v = xsum(lacc[k], 0.f).x;
-                if (wg == 0 && valid) logits[(size_t)row * n_cls + k] = v + __ldg(m.bf + k);
+                if (wg == 0 && valid) io.logits[k] = v + __ldg(m.bf + k);
             }
         }
         if constexpr (NWG > 1) ptx::named_bar_sync(2, THREADS);  // every aggregate update is in shared memory
         float tot = 0.f;
         for (int j = wg; j < m.d; j += NWG) tot += sAgg[j * 128 + lt];
         tot = xsum(tot, 0.f).x;
-        if (agg_out && valid) {
+        if (io.agg && valid) {
             const float inv = tot > 0.f ? 1.f / tot : 0.f;
-            for (int j = wg; j < m.d; j += NWG)
-                agg_out[(size_t)row * m.d + j] = tot > 0.f ? sAgg[j * 128 + lt] * inv : 0.f;
+            for (int j = wg; j < m.d; j += NWG) io.agg[j] = tot > 0.f ? sAgg[j * 128 + lt] * inv : 0.f;
         }
     }
 
@@ -895,16 +896,17 @@ int tc_patch(tabnet_model* m, Arena& a, const uint8_t* base, std::string* why) {
 }
 
 cudaError_t tc_launch(tabnet_model* m, const float* x_num, const int* x_cat, int64_t rows, float* logits,
-                      float* masks, float* agg, cudaStream_t stream) {
+                      float* masks, float* agg, cudaStream_t stream, const SegTable* seg) {
     TcParams p = m->tc;
-    p.num_tiles = (rows + 127) / 128;
+    p.seg = seg ? *seg : SegTable{nullptr, nullptr, 0};
     p.trace = nullptr;
 #ifdef TABNET_TRACE
     cudaHostGetDevicePointer((void**)&p.trace, tabnet_debug_trace_ptr(), 0);
 #endif
     const TcLaunch& L = m->tc_launch_cfg;
     const int64_t slots = (int64_t)m->num_sms * L.ctas_per_sm;
-    const unsigned grid = (unsigned)std::min<int64_t>(p.num_tiles, slots);
+    // a segmented launch learns its row count on the device: one CTA per slot
+    const unsigned grid = (unsigned)(seg ? slots : std::min<int64_t>((rows + 127) / 128, slots));
     const dim3 block(128 * L.nwg);
     const Variant v{p.m.N, L.nwg, m->precision == TABNET_BF16X3, L.zreg};
     const bool found = with_kernel(v, [&](auto fn) {

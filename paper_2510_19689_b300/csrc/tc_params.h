@@ -24,6 +24,7 @@ struct TcSmem {
 
 struct TcParams {
     ModelConsts m;
+    SegTable seg;              // segmented launch (seg.segs != nullptr) or one batch
     const uint8_t* wbase;      // packed weight chunks (device)
     const uint2* chunks;       // [chunks_per_tile] {byte offset from wbase, bytes}, stream order
     int chunks_per_tile;
@@ -43,7 +44,6 @@ struct TcParams {
     int n_slots;
     int slot_bytes;
     TcSmem sm;
-    int64_t num_tiles;
     unsigned* trace;           // debug builds only (TABNET_TRACE): progress words, else null
 };
 

@@ -33,7 +33,8 @@ EXPORTS = (
     "tabnet_abi_version", "tabnet_blob_inspect", "tabnet_create", "tabnet_dims_of",
     "tabnet_precision_of", "tabnet_forward", "tabnet_forward_host", "tabnet_poll_status",
     "tabnet_destroy", "tabnet_status_string", "tabnet_last_error", "tabnet_set_tile_config",
-    "tabnet_get_tile_config",
+    "tabnet_get_tile_config", "tabnet_forward_segments", "tabnet_forward_segments_device",
+    "tabnet_reserve_segments",
 )
 
 
@@ -41,6 +42,24 @@ class TabnetError(RuntimeError):
     def __init__(self, code: int, where: str, detail: str = ""):
         self.code = code
         super().__init__(f"{where}: {ERR.get(code, code)} ({detail})")
+
+
+class Segment(ctypes.Structure):
+    """tabnet_segment: one request's device buffers (48 bytes)."""
+    _fields_ = [
+        ("x_num", ctypes.c_void_p), ("x_cat", ctypes.c_void_p), ("rows", ctypes.c_int64),
+        ("logits", ctypes.c_void_p), ("step_masks", ctypes.c_void_p), ("agg_mask", ctypes.c_void_p),
+    ]
+
+
+def segment_array(segs):
+    """ctypes array of Segment from dicts {x_num, x_cat, rows, logits, masks, agg}
+    whose values are torch tensors, raw pointers or None."""
+    arr = (Segment * len(segs))()
+    for i, g in enumerate(segs):
+        arr[i] = Segment(_ptr(g.get("x_num")), _ptr(g.get("x_cat")), int(g["rows"]), _ptr(g.get("logits")),
+                         _ptr(g.get("masks")), _ptr(g.get("agg")))
+    return arr
 
 
 class Dims(ctypes.Structure):
@@ -79,6 +98,9 @@ def lib() -> ctypes.CDLL:
     L.tabnet_set_tile_config.argtypes = [vp, i32, i32, i32]
     ip = ctypes.POINTER(ctypes.c_int)
     L.tabnet_get_tile_config.argtypes = [vp, ip, ip, ip]
+    L.tabnet_forward_segments.argtypes = [vp, vp, i32, vp]
+    L.tabnet_forward_segments_device.argtypes = [vp, vp, i32, vp]
+    L.tabnet_reserve_segments.argtypes = [vp, i32]
     L.tabnet_destroy.argtypes = [vp]
     L.tabnet_destroy.restype = None
     L.tabnet_status_string.argtypes = [i32]
@@ -86,7 +108,8 @@ def lib() -> ctypes.CDLL:
     L.tabnet_last_error.restype = ctypes.c_char_p
     for name in ("tabnet_blob_inspect", "tabnet_create", "tabnet_dims_of", "tabnet_precision_of",
                  "tabnet_forward", "tabnet_forward_host", "tabnet_poll_status",
-                 "tabnet_set_tile_config", "tabnet_get_tile_config"):
+                 "tabnet_set_tile_config", "tabnet_get_tile_config", "tabnet_forward_segments",
+                 "tabnet_forward_segments_device", "tabnet_reserve_segments"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -164,6 +187,22 @@ class Model:
                                          _ptr(x_cat) if d.n_cat else None, rows, _ptr(lg),
                                          _ptr(mk), _ptr(ag), stream), "tabnet_forward_host")
         return lg, mk, ag
+
+    def forward_segments(self, segs, stream=None) -> None:
+        """Uneven request batches in one launch; segs: list of dicts (see
+        segment_array) or a ctypes Segment array in host memory."""
+        arr = segs if isinstance(segs, ctypes.Array) else segment_array(segs)
+        _check(lib().tabnet_forward_segments(self._h, ctypes.cast(arr, ctypes.c_void_p), len(arr),
+                                             _stream(stream)), "tabnet_forward_segments")
+
+    def forward_segments_device(self, dev_descriptors, n_segs: int, stream=None) -> None:
+        """Descriptors already in device memory (e.g. a uint8 CUDA tensor
+        holding n_segs Segment records); capturable in a CUDA graph."""
+        _check(lib().tabnet_forward_segments_device(self._h, _ptr(dev_descriptors), int(n_segs),
+                                                    _stream(stream)), "tabnet_forward_segments_device")
+
+    def reserve_segments(self, max_segs: int) -> None:
+        _check(lib().tabnet_reserve_segments(self._h, int(max_segs)), "tabnet_reserve_segments")
 
     def set_tile_config(self, nwg: int = 0, n_slots: int = 0, ctas_per_sm: int = 0) -> None:
         _check(lib().tabnet_set_tile_config(self._h, nwg, n_slots, ctas_per_sm), "tabnet_set_tile_config")
