@@ -177,6 +177,29 @@ int tabnet_forward_segments_device(tabnet_model* model, const tabnet_segment* se
  * Errors: ARG, OOM. */
 int tabnet_reserve_segments(tabnet_model* model, int max_segs);
 
+/* tabnet_forward_segments_device for callers that cannot allocate device
+ * memory.  (The paper has no counterpart: this is a deployment convenience of
+ * this library.)  Some callers must not call cudaMalloc once they are
+ * running: code that launches while a CUDA graph is being captured in the
+ * default (global) capture mode, where allocation calls are refused; serving
+ * processes that fix their device memory at start-up so that no request can
+ * fail or stall on an allocation; hosts that give a plug-in only memory they
+ * allocated themselves.  This entry point allocates nothing: the prefix sums
+ * of the segments' row counts (its only scratch) live in a fixed array in the
+ * library's device image, TABNET_NOALLOC_MAX_SEGMENTS + 1 entries (512 KB),
+ * held by every GPU that loads the library until the process exits.
+ *   segs    DEVICE array of n_segs descriptors (caller-owned, only read)
+ * The first call on a device looks up that array's device address (once per
+ * device, with the model's device made current for the call); make that
+ * first call before any stream capture.  Every call on a device shares the
+ * array: calls whose work overlaps on the GPU (other streams, other handles
+ * on the same device) race on it, so serialise them.  Nothing in the array
+ * has to start at zero: each launch rewrites the entries it reads.
+ * Errors: ARG (null, n_segs < 0 or > TABNET_NOALLOC_MAX_SEGMENTS), CUDA. */
+#define TABNET_NOALLOC_MAX_SEGMENTS 65536
+int tabnet_forward_segments_noalloc(tabnet_model* model, const tabnet_segment* segs, int n_segs,
+                                    void* stream);
+
 /* Same computation with HOST buffers (pinned or pageable): the inputs are
  * copied into a device workspace owned by the handle, the forward runs, and
  * the outputs are copied back, all on `stream`; the call returns after the

@@ -61,6 +61,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+int set_last_error(int code, const std::string& why) { return fail(code, why); }
+
 size_t Arena::add(const void* data, size_t bytes, size_t align) {
     size_t off = (image.size() + align - 1) / align * align;
     image.resize(off + bytes, 0);

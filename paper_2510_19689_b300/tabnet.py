@@ -34,8 +34,10 @@ EXPORTS = (
     "tabnet_precision_of", "tabnet_forward", "tabnet_forward_host", "tabnet_poll_status",
     "tabnet_destroy", "tabnet_status_string", "tabnet_last_error", "tabnet_set_tile_config",
     "tabnet_get_tile_config", "tabnet_forward_segments", "tabnet_forward_segments_device",
-    "tabnet_reserve_segments",
+    "tabnet_reserve_segments", "tabnet_forward_segments_noalloc",
 )
+#: fixed scratch capacity of tabnet_forward_segments_noalloc
+NOALLOC_MAX_SEGMENTS = 65536
 
 
 class TabnetError(RuntimeError):
@@ -101,6 +103,7 @@ def lib() -> ctypes.CDLL:
     L.tabnet_forward_segments.argtypes = [vp, vp, i32, vp]
     L.tabnet_forward_segments_device.argtypes = [vp, vp, i32, vp]
     L.tabnet_reserve_segments.argtypes = [vp, i32]
+    L.tabnet_forward_segments_noalloc.argtypes = [vp, vp, i32, vp]
     L.tabnet_destroy.argtypes = [vp]
     L.tabnet_destroy.restype = None
     L.tabnet_status_string.argtypes = [i32]
@@ -109,7 +112,8 @@ def lib() -> ctypes.CDLL:
     for name in ("tabnet_blob_inspect", "tabnet_create", "tabnet_dims_of", "tabnet_precision_of",
                  "tabnet_forward", "tabnet_forward_host", "tabnet_poll_status",
                  "tabnet_set_tile_config", "tabnet_get_tile_config", "tabnet_forward_segments",
-                 "tabnet_forward_segments_device", "tabnet_reserve_segments"):
+                 "tabnet_forward_segments_device", "tabnet_reserve_segments",
+                 "tabnet_forward_segments_noalloc"):
         getattr(L, name).restype = i32
     _lib = L
     return L
