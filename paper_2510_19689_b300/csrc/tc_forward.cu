@@ -56,7 +56,9 @@ namespace {
 constexpr uint64_t kWaitLimit = 1000000000ull;  // 1 s per wait
 constexpr float kSqrtHalf = 0.70710678118654752440f;
 constexpr int kMaxClasses = 8;
-constexpr int kZregChunks = 3;  // sparsemax input kept in registers up to 3 x 16 columns per thread
+constexpr int kFStride = 129;  // row stride (floats) of the input cache: transposed writes hit distinct banks
+// sparsemax input kept in registers: up to this many 16-column chunks per thread
+__host__ __device__ constexpr int zreg_chunks(int nwg) { return nwg == 1 ? 3 : 2; }
 
 #ifdef TABNET_TRACE
 #define TC_TRACE(i, v)                                                          \
@@ -69,6 +71,30 @@ constexpr int kZregChunks = 3;  // sparsemax input kept in registers up to 3 x 1
 #else
 #define TC_TRACE(i, v) \
     do {               \
+    } while (0)
+#endif
+
+#ifdef TABNET_TRACE
+#define PH_DECL unsigned long long ph_t = clock64(); unsigned long long ph_acc[16] = {0};
+#define PH_MARK(k)                          \
+    do {                                    \
+        const unsigned long long _t = clock64(); \
+        ph_acc[(k)] += _t - ph_t;           \
+        ph_t = _t;                          \
+    } while (0)
+#define PH_DUMP()                                                                                   \
+    do {                                                                                            \
+        if (p.trace && blockIdx.x == 0 && (lt % 32) == 0)                                           \
+            for (int _k = 0; _k < 16; ++_k)                                                         \
+                reinterpret_cast<volatile unsigned long long*>(p.trace + 1024)[(tid / 32) * 16 + _k] = ph_acc[_k]; \
+    } while (0)
+#else
+#define PH_DECL
+#define PH_MARK(k) \
+    do {           \
+    } while (0)
+#define PH_DUMP() \
+    do {          \
     } while (0)
 #endif
 
@@ -136,7 +162,7 @@ __device__ __forceinline__ float4 ld_epi(const float* g, uint32_t epi_s, int idx
 }
 
 template <int N, int NWG, bool SPLIT, bool ZREG>
-__global__ void __launch_bounds__(128 * NWG, 1)
+__global__ void __launch_bounds__(128 * NWG, (NWG == 2 && N <= 64) ? 2 : 1)
 tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* __restrict__ x_cat,
                   int64_t rows, float* __restrict__ logits, float* __restrict__ masks,
                   float* __restrict__ agg_out) {
@@ -144,6 +170,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     constexpr int CPW = N / NWG;  // GLU output columns per warpgroup
     constexpr int RCH = CPW / 16;  // 16-column chunks per thread
     constexpr int PARTS = SPLIT ? 2 : 1;  // weight chunks per 64-wide K block
+    constexpr int kZregChunks = zreg_chunks(NWG);
     static_assert(CPW % 16 == 0, "each warpgroup takes whole 16-column chunks");
 
     extern __shared__ uint8_t smem_raw[];
@@ -154,7 +181,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 
     uint8_t* sA = smem + p.sm.a_hi;
     uint8_t* sAlo = SPLIT ? smem + p.sm.a_lo : nullptr;
-    float* sAgg = reinterpret_cast<float*>(smem + p.sm.agg);
+    float* sAgg = reinterpret_cast<float*>(smem + (p.sm.agg >= 0 ? p.sm.agg : 0));
     float2* sX = reinterpret_cast<float2*>(smem + (p.sm.xch >= 0 ? p.sm.xch : 0));
     float* sWf = reinterpret_cast<float*>(smem + p.sm.wf);
     const uint32_t f_s = p.sm.fcache >= 0 ? ptx::smem_u32(smem + p.sm.fcache) : 0u;  // f cache (shared address)
@@ -181,6 +208,10 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         ptx::tmem_relinquish();
     }
     // model constants staged once per CTA
+    int* sColf = reinterpret_cast<int*>(smem + p.sm.colf);
+    for (int i = tid; i < p.dp; i += THREADS) sColf[i] = __ldg(p.col_feat + i);
+    uint2* sChunks = reinterpret_cast<uint2*>(smem + p.sm.chunks);
+    for (int i = tid; i < p.chunks_per_tile; i += THREADS) sChunks[i] = __ldg(p.chunks + i);
     for (int i = tid; i < m.n_classes * m.n_d; i += THREADS) sWf[i] = __ldg(m.wf + i);
     if (p.sm.epi >= 0)
         for (int i = tid; i < p.epi_floats / 4; i += THREADS)
@@ -190,33 +221,46 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     ptx::tc_fence_after();
     const uint32_t tmem = *sTmem;
     TC_TRACE(64 + tid / 32, 2);
+    PH_DECL
     const uint32_t t_acc = tmem + lane_off;
     const uint32_t t_p = t_acc + (uint32_t)p.tm_p;
     const uint32_t t_m = t_acc + (uint32_t)p.tm_m;
+    const bool agg_tmem = p.tm_agg >= 0;
+    const uint32_t t_agg = t_acc + (uint32_t)(agg_tmem ? p.tm_agg : 0);
 
     const int64_t total = total_rows(p.seg, rows);
     const int64_t num_tiles = (total + 127) / 128;
     const int64_t my_tiles =
         (int64_t)blockIdx.x < num_tiles ? (num_tiles - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t total_chunks = my_tiles * p.chunks_per_tile;
-    int64_t g_issue = 0, g_cons = 0;   // thread 0 only
-    bool acc_outstanding = false;      // thread 0 only
+    // Ring bookkeeping (thread 0 only), incremental so that no 64-bit
+    // division sits on the MMA critical path: chunk g of the CTA's stream
+    // goes to slot g mod S in round g / S, and is chunk g mod chunks_per_tile
+    // of a tile's sequence.
+    int64_t g_issue = 0, g_cons = 0;  // chunks issued / consumed so far
+    int is_slot = 0, is_chunk = 0;    // slot and per-tile index of chunk g_issue
+    uint32_t is_round = 0;            // round of chunk g_issue
+    int cs_slot = 0;                  // slot of chunk g_cons
+    uint32_t cs_round = 0;            // round of chunk g_cons
+    bool acc_outstanding = false;
     uint32_t acc_phase = 0;
     int xc = 0;
     int lc = 0;  // layers run by this CTA
 
-    // Thread 0: start the copy of chunk g_issue once its slot is free.
+    // Thread 0: start the copy of chunk g_issue once its slot is free (its
+    // previous occupant, round is_round - 1, has been read by the MMAs).
     auto issue_next = [&]() -> bool {
-        const int64_t g = g_issue;
-        const int slot = (int)(g % S);
-        if (g >= S && !ptx::mbar_wait(bar_empty + 8 * slot, (uint32_t)(((g / S) - 1) & 1), kWaitLimit)) {
-            note_timeout(m.status, 5, (unsigned)g);
+        const int slot = is_slot;
+        if (is_round > 0 && !ptx::mbar_wait(bar_empty + 8 * slot, (is_round - 1) & 1u, kWaitLimit)) {
+            note_timeout(m.status, 5, (unsigned)g_issue);
             return false;
         }
-        const uint2 ck = p.chunks[g % p.chunks_per_tile];
+        const uint2 ck = sChunks[is_chunk];
         ptx::mbar_arrive_expect_tx(bar_full + 8 * slot, ck.y);
         ptx::bulk_g2s(ring_base + (uint32_t)(slot * p.slot_bytes), p.wbase + ck.x, ck.y, bar_full + 8 * slot);
         ++g_issue;
+        if (++is_chunk == p.chunks_per_tile) is_chunk = 0;
+        if (++is_slot == S) { is_slot = 0; ++is_round; }
         return true;
     };
     if (tid == 0)
@@ -226,6 +270,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     // run one layer's MMA chain (kblocks 64-wide K blocks, kb K steps of 16)
     // and wait for the accumulator.  Returns false when the CTA has to stop.
     auto run_mma = [&](int kblocks, int kb, uint32_t idesc) -> bool {
+        PH_MARK(7);
         ptx::fence_proxy_async();
         ptx::tc_fence_before();
         __syncthreads();
@@ -235,51 +280,81 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             int kk = 0;
             bool ok = true;
             for (int b = 0; b < kblocks && ok; ++b) {
-                const int64_t g = g_cons;
-                while (ok && g_issue < g + PARTS) ok = issue_next();
+                while (ok && g_issue < g_cons + PARTS) ok = issue_next();
+                // slots (and rounds) of this K block's hi and lo chunks
+                int slot_p[PARTS];
+                uint32_t round_p[PARTS];
+                {
+                    int sl = cs_slot;
+                    uint32_t rd = cs_round;
+#pragma unroll
+                    for (int part = 0; part < PARTS; ++part) {
+                        slot_p[part] = sl;
+                        round_p[part] = rd;
+                        if (++sl == S) { sl = 0; ++rd; }
+                    }
+                }
+                PH_MARK(12);
                 for (int part = 0; part < PARTS && ok; ++part) {
-                    const int64_t gp = g + part;
-                    if (!ptx::mbar_wait(bar_full + 8 * (int)(gp % S), (uint32_t)((gp / S) & 1), kWaitLimit)) {
-                        note_timeout(m.status, 1, (unsigned)gp);
+                    if (!ptx::mbar_wait(bar_full + 8 * slot_p[part], round_p[part] & 1u, kWaitLimit)) {
+                        note_timeout(m.status, 1, (unsigned)(g_cons + part));
                         ok = false;
                     }
                 }
+                PH_MARK(13);
                 if (!ok) break;
-                const uint32_t b_hi = ring_base + (uint32_t)((int)(g % S) * p.slot_bytes);
-                const uint32_t b_lo = ring_base + (uint32_t)((int)((g + 1) % S) * p.slot_bytes);
-                const uint32_t a_hi = a_base + (uint32_t)(b * 16384);
-                const uint32_t a_lo = alo_base + (uint32_t)(b * 16384);
-#pragma unroll 1
-                for (int k4 = 0; k4 < 4 && kk < kb; ++k4, ++kk) {
-                    ptx::mma_f16(tmem, ptx::sw128_desc(a_hi + 32 * k4), ptx::sw128_desc(b_hi + 32 * k4), idesc,
-                                 kk > 0 ? 1u : 0u);
-                    if constexpr (SPLIT) {
-                        ptx::mma_f16(tmem, ptx::sw128_desc(a_hi + 32 * k4), ptx::sw128_desc(b_lo + 32 * k4), idesc, 1u);
-                        ptx::mma_f16(tmem, ptx::sw128_desc(a_lo + 32 * k4), ptx::sw128_desc(b_hi + 32 * k4), idesc, 1u);
+                // descriptors of the block's first K step; a K step of 16
+                // bf16 (32 bytes) adds 2 to the encoded start address
+                const uint64_t d_bhi = ptx::sw128_desc(ring_base + (uint32_t)(slot_p[0] * p.slot_bytes));
+                const uint64_t d_blo = ptx::sw128_desc(ring_base + (uint32_t)(slot_p[PARTS - 1] * p.slot_bytes));
+                const uint64_t d_ahi = ptx::sw128_desc(a_base + (uint32_t)(b * 16384));
+                const uint64_t d_alo = ptx::sw128_desc(alo_base + (uint32_t)(b * 16384));
+                const int nk = min(4, kb - kk);
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    if (k4 < nk) {
+                        const uint64_t step = 2u * (uint32_t)k4;
+                        ptx::mma_f16(tmem, d_ahi + step, d_bhi + step, idesc, (kk + k4) > 0 ? 1u : 0u);
+                        if constexpr (SPLIT) {
+                            ptx::mma_f16(tmem, d_ahi + step, d_blo + step, idesc, 1u);
+                            ptx::mma_f16(tmem, d_alo + step, d_bhi + step, idesc, 1u);
+                        }
                     }
                 }
-                for (int part = 0; part < PARTS; ++part) ptx::mma_commit(bar_empty + 8 * (int)((g + part) % S));
+                kk += nk;
+#pragma unroll
+                for (int part = 0; part < PARTS; ++part) ptx::mma_commit(bar_empty + 8 * slot_p[part]);
                 g_cons += PARTS;
+#pragma unroll
+                for (int part = 0; part < PARTS; ++part)
+                    if (++cs_slot == S) { cs_slot = 0; ++cs_round; }
             }
             ptx::mma_commit(bar_acc);
+            PH_MARK(9);
             acc_outstanding = true;
             if (!ok) *sAbort = 1;
-        }
-        const bool got = ptx::mbar_wait(bar_acc, acc_phase, kWaitLimit);
-        acc_phase ^= 1;
-        ptx::tc_fence_after();
-        if (!got) {
-            *sAbort = 1;
-            note_timeout(m.status, 2, (unsigned)lc);
-        }
-        ++lc;
-        if (tid == 0) {
-            if (got) acc_outstanding = false;
+
+            // Only this thread waits on the accumulator barrier; the others
+            // park on the CTA barrier below, which costs no issue slots.
+            const bool got = ptx::mbar_wait(bar_acc, acc_phase, kWaitLimit);
+            PH_MARK(10);
+            if (got) {
+                acc_outstanding = false;
+            } else {
+                *sAbort = 1;
+                note_timeout(m.status, 2, (unsigned)lc);
+            }
             // every MMA so far has completed: refill the free slots
             if (!*sAbort)
                 while (g_issue < total_chunks && g_issue < g_cons + S)
                     if (!issue_next()) { *sAbort = 1; break; }
+            PH_MARK(11);
         }
+        acc_phase ^= 1;
+        ++lc;
+        __syncthreads();
+        ptx::tc_fence_after();
+        PH_MARK(1);
         return true;
     };
 
@@ -329,21 +404,83 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         };
 
         // ---- tile start: f -> A (K = dp), P = 1, aggregate = 0
+        float* fc = reinterpret_cast<float*>(smem + (f_s ? p.sm.fcache : 0));
+        if (f_s) {
+            // Gather the tile's inputs cooperatively: warp w takes 128/(4 NWG)
+            // rows, its lanes walk the columns (coalesced reads of a row),
+            // all rows' loads in flight before any use.
+            constexpr int RPW = 128 / (4 * NWG);
+            const float** sRowX = reinterpret_cast<const float**>(smem + p.sm.rowp);
+            const int** sRowC = reinterpret_cast<const int**>(smem + p.sm.rowp + 128 * 8);
+            float** sRowM = reinterpret_cast<float**>(smem + p.sm.rowp + 128 * 16);
+            if (wg == 0) {
+                sRowX[lt] = valid ? io.x_num : nullptr;
+                sRowC[lt] = valid ? io.x_cat : nullptr;
+                sRowM[lt] = valid ? io.masks : nullptr;
+            }
+            __syncthreads();
+            const int lane = tid & 31, r0 = warp * RPW;
+            for (int cb = 0; cb < m.n_num; cb += 32) {
+                const int c = cb + lane;
+                float xv[RPW];
+#pragma unroll
+                for (int i = 0; i < RPW; ++i) {
+                    const float* xr = sRowX[r0 + i];
+                    xv[i] = (c < m.n_num && xr) ? __ldg(xr + c) : 0.f;
+                }
+                if (c < m.n_num) {
+                    const float s0 = __ldg(m.s0 + c), t0 = __ldg(m.t0 + c);
+#pragma unroll
+                    for (int i = 0; i < RPW; ++i) fc[c * kFStride + r0 + i] = fmaf(s0, xv[i], t0);
+                }
+            }
+            for (int jb = 0; jb < m.n_cat; jb += 32) {
+                const int j = jb + lane;
+                int iv[RPW];
+#pragma unroll
+                for (int i = 0; i < RPW; ++i) {
+                    const int* cr = sRowC[r0 + i];
+                    iv[i] = (j < m.n_cat && cr) ? __ldg(cr + j) : 0;
+                }
+                if (j < m.n_cat) {
+                    const int card = __ldg(m.cat_card + j);
+                    const int c0 = __ldg(m.feat_col + m.n_num + j), len = __ldg(m.feat_len + m.n_num + j);
+                    const float* tab = m.emb + __ldg(m.cat_off + j);
+#pragma unroll
+                    for (int i = 0; i < RPW; ++i) {
+                        const bool oob = iv[i] < 0 || iv[i] >= card;
+                        if (oob && sRowC[r0 + i]) atomicOr(m.status, TABNET_STATUS_CAT_OOB);
+                        for (int e = 0; e < len; ++e)
+                            fc[(c0 + e) * kFStride + r0 + i] =
+                                oob ? __ldg(m.t0 + c0 + e) : __ldg(tab + (size_t)iv[i] * len + e);
+                    }
+                }
+            }
+            __syncthreads();
+        }
         for (int ch = wg; ch < dch; ch += NWG) {
             float v[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                v[j] = f_value(ch * 16 + j, valid);
-                if (f_s) reinterpret_cast<float*>(smem + p.sm.fcache)[(ch * 16 + j) * 128 + lt] = v[j];
+                const int c = ch * 16 + j;
+                v[j] = f_s ? (c < de ? fc[c * kFStride + lt] : 0.f) : f_value(c, valid);
             }
             store_a16<SPLIT>(sA, sAlo, lt, ch, v);
             uint32_t ones[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) ones[j] = 0x3f800000u;
             ptx::tmem_st16(t_p + ch * 16, ones);
+            if (agg_tmem) {
+                uint32_t zeros[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) zeros[j] = 0u;
+                ptx::tmem_st16(t_agg + ch * 16, zeros);
+            }
         }
-        for (int j = wg; j < m.d; j += NWG) sAgg[j * 128 + lt] = 0.f;
+        if (!agg_tmem)
+            for (int j = wg; j < m.d; j += NWG) sAgg[j * 128 + lt] = 0.f;
         ptx::tmem_wait_st();
+        PH_MARK(0);
         float lacc[kMaxClasses];
 #pragma unroll
         for (int k = 0; k < kMaxClasses; ++k) lacc[k] = 0.f;
@@ -353,8 +490,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             if (s > 0) {
                 // ---- attentive transformer of step s: z = (W_att a) * scale + shift, times P
                 if (!run_mma(p.kn_blocks, N / 16, idesc_att)) { alive = false; break; }
-                const int asc = n_ft_layers * 4 * N + (s - 1) * 2 * p.dp;  // float index of the scale
-                const int ash = asc + p.dp;
+                const int ash = n_ft_layers * 2 * N + (s - 1) * p.dp;  // float index of the BN shift
                 auto load_z = [&](int ch, float (&z)[16], uint32_t (&pr)[16]) {
                     uint32_t acc[16];
                     ptx::tmem_ld16(t_acc + ch * 16, acc);
@@ -362,15 +498,13 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     ptx::tmem_wait_ld(acc, pr);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 a = ld_epi(epi, epi_s, asc + ch * 16 + 4 * q);
                         const float4 b = ld_epi(epi, epi_s, ash + ch * 16 + 4 * q);
-                        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+                        const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
                         for (int t = 0; t < 4; ++t) {
                             const int j = 4 * q + t;
-                            z[j] = (ch * 16 + j < de)
-                                       ? fmaf(__uint_as_float(acc[j]), av[t], bv[t]) * __uint_as_float(pr[j])
-                                       : -INFINITY;
+                            z[j] = (ch * 16 + j < de) ? (__uint_as_float(acc[j]) + bv[t]) * __uint_as_float(pr[j])
+                                                      : -INFINITY;
                         }
                     }
                 };
@@ -445,8 +579,10 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     }
                 }
                 TC_TRACE(128 + tid / 32, 4000 + lc);
+                PH_MARK(2);
                 // Mask, prior, masked input (A for the step's first FC), outputs.
                 float* mrow = (io.masks && valid) ? io.masks + (size_t)(s - 1) * de : nullptr;
+                float* mst = p.sm.mstage >= 0 ? reinterpret_cast<float*>(smem + p.sm.mstage) : nullptr;
 #pragma unroll 1
                 for (int il = 0; wg + il * NWG < dch; ++il) {
                     const int ch = wg + il * NWG;
@@ -484,15 +620,47 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     for (int j = 0; j < 16; ++j) {
                         const int c = ch * 16 + j;
                         if (f_s) {
-                            v[j] = mk[j] * ptx::ld_shared_f32(f_s + 4u * (uint32_t)(c * 128 + lt));
+                            v[j] = c < de ? mk[j] * ptx::ld_shared_f32(f_s + 4u * (uint32_t)(c * kFStride + lt)) : 0.f;
                         } else {
                             v[j] = (c < de && mk[j] > 0.f) ? mk[j] * f_value(c, false) : 0.f;
                         }
-                        if (mrow && c < de) mrow[c] = mk[j];
+                    }
+                    if (mst) {
+                        // staged: written out row by row below
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (ch * 16 + j < de) mst[(ch * 16 + j) * kFStride + lt] = mk[j];
+                    } else if (mrow) {
+                        if (((de & 3) == 0) && ((reinterpret_cast<uintptr_t>(mrow) & 15) == 0) && ch * 16 + 16 <= de) {
+                            float4* d4 = reinterpret_cast<float4*>(mrow + ch * 16);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                d4[q] = make_float4(mk[4 * q], mk[4 * q + 1], mk[4 * q + 2], mk[4 * q + 3]);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (ch * 16 + j < de) mrow[ch * 16 + j] = mk[j];
+                        }
                     }
                     store_a16<SPLIT>(sA, sAlo, lt, ch, v);
                 }
                 ptx::tmem_wait_st();
+                if (mst) {
+                    // every warp writes whole rows: lanes walk a row's columns
+                    __syncthreads();
+                    constexpr int RPW = 128 / (4 * NWG);
+                    float** sRowM = reinterpret_cast<float**>(smem + p.sm.rowp + 128 * 16);
+                    const int lane = tid & 31;
+                    for (int i = 0; i < RPW; ++i) {
+                        const int r = warp * RPW + i;
+                        float* dst = sRowM[r];
+                        if (dst) {
+                            dst += (size_t)(s - 1) * de;
+                            for (int c = lane; c < de; c += 32) dst[c] = mst[c * kFStride + r];
+                        }
+                    }
+                }
+                PH_MARK(3);
             }
 
             // ---- feature transformer s
@@ -502,38 +670,48 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     alive = false;
                     break;
                 }
-                const int sc = (s * lpf + l) * 4 * N;  // float index of the layer's scale
-                const int sh = sc + 2 * N;
+                const int sh = (s * lpf + l) * 2 * N;  // float index of the layer's BN shift
                 TC_TRACE(128 + tid / 32, 3000 + lc);
+                // TMEM loads run one chunk ahead of the arithmetic: chunk cc+1
+                // is requested before chunk cc is computed, and waited for after.
+                uint32_t lin[2][16], gat[2][16];
+                ptx::tmem_ld16(t_acc + wg * CPW, lin[0]);
+                ptx::tmem_ld16(t_acc + N + wg * CPW, gat[0]);
+                ptx::tmem_wait_ld(lin[0], gat[0]);
 #pragma unroll
                 for (int cc = 0; cc < RCH; ++cc) {
                     const int c0 = wg * CPW + cc * 16;
-                    uint32_t lin[16], gat[16];
-                    ptx::tmem_ld16(t_acc + c0, lin);
-                    ptx::tmem_ld16(t_acc + N + c0, gat);
-                    ptx::tmem_wait_ld(lin, gat);
+                    const int cur = cc & 1;
+                    if (cc + 1 < RCH) {
+                        ptx::tmem_ld16(t_acc + c0 + 16, lin[cur ^ 1]);
+                        ptx::tmem_ld16(t_acc + N + c0 + 16, gat[cur ^ 1]);
+                    }
+                    float4 hl4[4], hg4[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        hl4[q] = ld_epi(epi, epi_s, sh + c0 + 4 * q);
+                        hg4[q] = ld_epi(epi, epi_s, sh + N + c0 + 4 * q);
+                    }
                     float out[16];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 sl = ld_epi(epi, epi_s, sc + c0 + 4 * q);
-                        const float4 hl = ld_epi(epi, epi_s, sh + c0 + 4 * q);
-                        const float4 sg = ld_epi(epi, epi_s, sc + N + c0 + 4 * q);
-                        const float4 hg = ld_epi(epi, epi_s, sh + N + c0 + 4 * q);
-                        const float slv[4] = {sl.x, sl.y, sl.z, sl.w}, hlv[4] = {hl.x, hl.y, hl.z, hl.w};
-                        const float sgv[4] = {sg.x, sg.y, sg.z, sg.w}, hgv[4] = {hg.x, hg.y, hg.z, hg.w};
+                        const float hlv[4] = {hl4[q].x, hl4[q].y, hl4[q].z, hl4[q].w};
+                        const float hgv[4] = {hg4[q].x, hg4[q].y, hg4[q].z, hg4[q].w};
 #pragma unroll
                         for (int t = 0; t < 4; ++t) {
                             const int j = 4 * q + t;
-                            const float ul = fmaf(__uint_as_float(lin[j]), slv[t], hlv[t]);
-                            const float ug = fmaf(__uint_as_float(gat[j]), sgv[t], hgv[t]);
+                            const float ul = __uint_as_float(lin[cur][j]) + hlv[t];
+                            const float ug = __uint_as_float(gat[cur][j]) + hgv[t];
                             const float g = ul * (SPLIT ? sigmoid_accurate(ug) : sigmoid_fast(ug));
                             const float x = first ? g : (res[cc][j] + g) * kSqrtHalf;
                             res[cc][j] = x;
                             out[j] = x;
                         }
                     }
+                    if (cc + 1 < RCH) ptx::tmem_wait_ld(lin[cur ^ 1], gat[cur ^ 1]);
                     store_a16<SPLIT>(sA, sAlo, lt, c0 / 16, out);
                 }
+                PH_MARK(4);
             }
             if (!alive) break;
 
@@ -549,12 +727,32 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                             const float dv = fmaxf(res[cc][j], 0.f);
                             eta += dv;
 #pragma unroll
-                            for (int k = 0; k < kMaxClasses; ++k)
-                                if (k < n_cls) lacc[k] = fmaf(sWf[k * n_d + c], dv, lacc[k]);
+                            for (int k = 0; k < kMaxClasses; ++k) {
+                                if (k >= n_cls) break;
+                                lacc[k] = fmaf(sWf[k * n_d + c], dv, lacc[k]);
+                            }
                         }
                     }
                 }
                 eta = xsum(eta, 0.f).x;
+                if (agg_tmem) {
+                    for (int ch = wg; ch < dch; ch += NWG) {
+                        uint32_t mh[8], ag[16];
+                        ptx::tmem_ld8(t_m + ch * 8, mh);
+                        ptx::tmem_ld16(t_agg + ch * 16, ag);
+                        ptx::tmem_wait_ld(ag);
+                        asm volatile("" : "+r"(mh[0]), "+r"(mh[1]), "+r"(mh[2]), "+r"(mh[3]), "+r"(mh[4]),
+                                     "+r"(mh[5]), "+r"(mh[6]), "+r"(mh[7]));
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float2 mm = __half22float2(*reinterpret_cast<__half2*>(&mh[j]));
+                            ag[2 * j] = __float_as_uint(fmaf(eta, mm.x, __uint_as_float(ag[2 * j])));
+                            ag[2 * j + 1] = __float_as_uint(fmaf(eta, mm.y, __uint_as_float(ag[2 * j + 1])));
+                        }
+                        ptx::tmem_st16(t_agg + ch * 16, ag);
+                    }
+                    ptx::tmem_wait_st();
+                } else
                 for (int ch = wg; ch < dch; ch += NWG) {
                     uint32_t mh[8];
                     ptx::tmem_ld8(t_m + ch * 8, mh);
@@ -567,13 +765,14 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                         for (int t = 0; t < 2; ++t) {
                             const int c = ch * 16 + 2 * j + t;
                             if (c < de && mv[t] > 0.f) {
-                                float* dst = sAgg + __ldg(p.col_feat + c) * 128 + lt;
+                                float* dst = sAgg + sColf[c] * 128 + lt;
                                 if constexpr (NWG == 1) *dst = fmaf(eta, mv[t], *dst);
                                 else atomicAdd(dst, eta * mv[t]);
                             }
                         }
                     }
                 }
+                PH_MARK(5);
             }
         }
         if (!alive) break;
@@ -586,23 +785,53 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 if (wg == 0 && valid) io.logits[k] = v + __ldg(m.bf + k);
             }
         }
-        if constexpr (NWG > 1) ptx::named_bar_sync(2, THREADS);  // every aggregate update is in shared memory
-        float tot = 0.f;
-        for (int j = wg; j < m.d; j += NWG) tot += sAgg[j * 128 + lt];
-        tot = xsum(tot, 0.f).x;
-        if (io.agg && valid) {
+        if (agg_tmem) {
+            // one column per feature: normalise the TMEM aggregate directly
+            float tot = 0.f;
+            for (int ch = wg; ch < dch; ch += NWG) {
+                uint32_t ag[16];
+                ptx::tmem_ld16(t_agg + ch * 16, ag);
+                ptx::tmem_wait_ld(ag);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (ch * 16 + j < de) tot += __uint_as_float(ag[j]);
+            }
+            tot = xsum(tot, 0.f).x;
             const float inv = tot > 0.f ? 1.f / tot : 0.f;
-            for (int j = wg; j < m.d; j += NWG) io.agg[j] = tot > 0.f ? sAgg[j * 128 + lt] * inv : 0.f;
+            for (int ch = wg; ch < dch; ch += NWG) {
+                uint32_t ag[16];
+                ptx::tmem_ld16(t_agg + ch * 16, ag);
+                ptx::tmem_wait_ld(ag);
+                if (io.agg && valid) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (ch * 16 + j < de) io.agg[ch * 16 + j] = tot > 0.f ? __uint_as_float(ag[j]) * inv : 0.f;
+                }
+            }
+        } else {
+            if constexpr (NWG > 1) ptx::named_bar_sync(2, THREADS);  // every aggregate update is in shared memory
+            float tot = 0.f;
+            for (int j = wg; j < m.d; j += NWG) tot += sAgg[j * 128 + lt];
+            tot = xsum(tot, 0.f).x;
+            if (io.agg && valid) {
+                const float inv = tot > 0.f ? 1.f / tot : 0.f;
+                for (int j = wg; j < m.d; j += NWG) io.agg[j] = tot > 0.f ? sAgg[j * 128 + lt] * inv : 0.f;
+            }
         }
+        PH_MARK(6);
     }
+    PH_DUMP();
 
     // ---- teardown: no copy or MMA may still target this CTA's memory
     TC_TRACE(96 + tid / 32, 900000 + lc);
     __syncthreads();
     if (tid == 0) {
-        for (int64_t g = g_cons; g < g_issue; ++g)
-            if (!ptx::mbar_wait(bar_full + 8 * (int)(g % S), (uint32_t)((g / S) & 1), kWaitLimit))
-                note_timeout(m.status, 3, (unsigned)g);
+        int sl = cs_slot;
+        uint32_t rd = cs_round;
+        for (int64_t g = g_cons; g < g_issue; ++g) {
+            if (!ptx::mbar_wait(bar_full + 8 * sl, rd & 1u, kWaitLimit)) note_timeout(m.status, 3, (unsigned)g);
+            if (++sl == S) { sl = 0; ++rd; }
+        }
         if (acc_outstanding && !ptx::mbar_wait(bar_acc, acc_phase ^ 1, kWaitLimit))
             note_timeout(m.status, 4, (unsigned)lc);
     }
@@ -685,8 +914,8 @@ bool with_kernel(const Variant& v, F&& f) {
     return false;
 }
 
-TcSmem smem_layout(int N, int dp, int d, int n_cls, int n_d, int n_slots, int slot_bytes, bool split, int nwg,
-                   int epi_floats, bool with_epi, bool with_f) {
+TcSmem smem_layout(int N, int dp, int de, int d, int n_cls, int n_d, int n_slots, int slot_bytes, bool split,
+                   int nwg, int epi_floats, int n_chunks, bool agg_tmem, bool with_epi, bool with_f, bool with_mst) {
     TcSmem s{};
     const int a_blocks = (std::max(dp, N) + 63) / 64;
     int o = 0;
@@ -694,14 +923,23 @@ TcSmem smem_layout(int N, int dp, int d, int n_cls, int n_d, int n_slots, int sl
     s.a_lo = -1;
     if (split) { s.a_lo = o; o += a_blocks * 16384; }
     s.ring = o; o += n_slots * slot_bytes;
-    s.agg = o; o += round_up(d * 128 * 4, 16);
+    s.agg = -1;
+    if (!agg_tmem) { s.agg = o; o += round_up(d * 128 * 4, 16); }
     s.xch = -1;
     if (nwg > 1) { s.xch = o; o += 2 * 2 * 128 * 8; }
     s.wf = o; o += round_up(n_cls * n_d * 4, 16);
     s.epi = -1;
     if (with_epi) { s.epi = o; o += round_up(epi_floats * 4, 16); }
     s.fcache = -1;
-    if (with_f) { s.fcache = o; o += dp * 128 * 4; }
+    s.rowp = -1;
+    s.mstage = -1;
+    if (with_f) {
+        s.fcache = o; o += round_up(de * kFStride * 4, 16);
+        s.rowp = o; o += 128 * 24;
+        if (with_mst) { s.mstage = o; o += round_up(de * kFStride * 4, 16); }
+    }
+    s.colf = o; o += round_up(dp * 4, 16);
+    s.chunks = o; o += round_up(n_chunks * 8, 16);
     s.bar = o; o += round_up((2 * n_slots + 3) * 8, 16);
     s.total = o;
     return s;
@@ -731,9 +969,17 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
     if (cols > 512) { *why = "TMEM budget exceeded"; return TABNET_ERR_UNSUPPORTED_DIMS; }
     TcParams& p = m->tc;
     p.dp = dp;
-    p.tmem_cols = cols;
     p.tm_p = accw;
     p.tm_m = accw + dp;
+    // the aggregate lives in TMEM when every feature is one embedded column
+    // and dp more columns fit in the allocation (or the next, <= 256)
+    p.tm_agg = -1;
+    if (d.d_emb == d.n_feat) {
+        int c2 = 32;
+        while (c2 < need + dp) c2 *= 2;
+        if (c2 <= std::max(cols, 256)) { p.tm_agg = need; cols = c2; }
+    }
+    p.tmem_cols = cols;
     p.k0_blocks = (dp + 63) / 64;
     p.kn_blocks = (N + 63) / 64;
 
@@ -752,9 +998,15 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
                 keep->push_back({off, cb});
             }
     };
-    std::vector<std::vector<std::pair<size_t, uint32_t>>> shared_chunks(d.n_shared);
-    for (int l = 0; l < d.n_shared; ++l)
-        push_layer(hm.shared_fc[l].data(), 2 * N, l == 0 ? d.d_emb : N, 0, l == 0 ? dp : N, &shared_chunks[l]);
+    // BN scale is folded into the packed weights (W' = diag(scale) W, rounded
+    // after scaling, so a shared layer gets one packed copy per feature
+    // transformer); the epilogue adds the BN shift only.
+    auto scaled = [](const std::vector<float>& W, const std::vector<float>& sc, int rows, int k) {
+        std::vector<float> w((size_t)rows * k);
+        for (int r = 0; r < rows; ++r)
+            for (int c = 0; c < k; ++c) w[(size_t)r * k + c] = (float)((double)sc[r] * W[(size_t)r * k + c]);
+        return w;
+    };
     std::vector<std::pair<size_t, uint32_t>> stream;
     std::vector<float> epi, att_epi;
     for (int s = 0; s <= d.n_steps; ++s) {
@@ -762,26 +1014,21 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
             // attentive FC [de, n_a] acting on the whole FT output [N] as
             // [dp, N]: columns [0, n_d) (the decision part) and rows beyond
             // de (padding) carry zero weight
-            std::vector<float> wp((size_t)dp * d.n_a, 0.f);
-            std::memcpy(wp.data(), hm.att_fc[s - 1].data(), sizeof(float) * d.d_emb * d.n_a);
-            push_layer(wp.data(), dp, d.n_a, d.n_d, N, &stream);
             std::vector<float> sc, sh;
             fold_bn(hm.att_bn[s - 1], d.bn_eps, sc, sh);
-            sc.resize(dp, 0.f);
+            std::vector<float> wp((size_t)dp * d.n_a, 0.f);
+            const std::vector<float> ws = scaled(hm.att_fc[s - 1], sc, d.d_emb, d.n_a);
+            std::memcpy(wp.data(), ws.data(), sizeof(float) * d.d_emb * d.n_a);
+            push_layer(wp.data(), dp, d.n_a, d.n_d, N, &stream);
             sh.resize(dp, 0.f);
-            att_epi.insert(att_epi.end(), sc.begin(), sc.end());
             att_epi.insert(att_epi.end(), sh.begin(), sh.end());
         }
         for (int l = 0; l < d.n_shared + d.n_indep; ++l) {
             GluLayer g = hm.layer(s, l);
-            if (l < d.n_shared) {
-                stream.insert(stream.end(), shared_chunks[l].begin(), shared_chunks[l].end());
-            } else {
-                push_layer(g.w->data(), 2 * N, g.k, 0, l == 0 ? dp : N, &stream);
-            }
             std::vector<float> sc, sh;
             fold_bn(*g.bn, d.bn_eps, sc, sh);
-            epi.insert(epi.end(), sc.begin(), sc.end());
+            const std::vector<float> ws = scaled(*g.w, sc, 2 * N, g.k);
+            push_layer(ws.data(), 2 * N, g.k, 0, l == 0 ? dp : N, &stream);
             epi.insert(epi.end(), sh.begin(), sh.end());
         }
     }
@@ -819,7 +1066,7 @@ int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std
     if (N == 16 && nwg != 1) { *why = "N = 16 takes one warpgroup"; return TABNET_ERR_UNSUPPORTED_DIMS; }
     if (nwg != 1 && nwg != 2) { *why = "one or two warpgroups"; return TABNET_ERR_UNSUPPORTED_DIMS; }
     const int dch = p.dp / 16;
-    const bool zreg = (dch + nwg - 1) / nwg <= kZregChunks;
+    const bool zreg = (dch + nwg - 1) / nwg <= zreg_chunks(nwg);
     const Variant v{N, nwg, split, zreg};
     cudaFuncAttributes fa{};
     if (!with_kernel(v, [&](auto fn) { cudaFuncGetAttributes(&fa, fn); })) {
@@ -837,35 +1084,38 @@ int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std
     const int min_slots = split ? 2 : 1;
     int cps_max = std::max(1, std::min({tmem_limit, reg_limit, 4}));
     int best_cps = 0, best_slots = 0;
-    bool best_epi = false, best_f = false;
+    bool best_epi = false, best_f = false, best_mst = false;
+    // Per CTA count (most first): stage the BN shifts and the tile's input in
+    // shared memory when they fit, then take the deepest ring (<= 6) left.
     for (int cps = cps_max; cps >= 1 && !best_cps; --cps) {
         if (ctas_per_sm > 0 && cps != ctas_per_sm) continue;
         const size_t per_cta = (size_t)dev_smem_sm / cps - reserved;
         const size_t budget = std::min((size_t)m->smem_optin, per_cta) - 1024;
-        for (int sl = 8; sl >= min_slots; --sl) {
-            if (n_slots > 0 && sl != n_slots) continue;
-            TcSmem s = smem_layout(N, p.dp, d.n_feat, d.n_classes, d.n_d, sl, slot_bytes, split, nwg, p.epi_floats,
-                                   false, false);
-            if ((size_t)s.total > budget) continue;
-            // with several CTAs per SM keep at least two layers' chunks in flight
-            const int want = split ? 4 : 2;
-            if (n_slots <= 0 && ctas_per_sm <= 0 && cps > 1 && sl < want) break;
-            best_cps = cps;
-            best_slots = sl;
-            TcSmem se = smem_layout(N, p.dp, d.n_feat, d.n_classes, d.n_d, sl, slot_bytes, split, nwg,
-                                    p.epi_floats, true, false);
-            best_epi = (size_t)se.total <= budget;
-            TcSmem sf = smem_layout(N, p.dp, d.n_feat, d.n_classes, d.n_d, sl, slot_bytes, split, nwg,
-                                    p.epi_floats, best_epi, true);
-            best_f = (size_t)sf.total <= budget;
-            break;
+        const bool stage_opts[6][3] = {{true, true, true},  {true, true, false},  {true, false, false},
+                                       {false, true, true}, {false, true, false}, {false, false, false}};
+        for (const auto& st : stage_opts) {
+            int found = 0;
+            for (int sl = 6; sl >= min_slots; --sl) {
+                if (n_slots > 0 && sl != n_slots) continue;
+                TcSmem sm = smem_layout(N, p.dp, d.d_emb, d.n_feat, d.n_classes, d.n_d, sl, slot_bytes, split, nwg,
+                                        p.epi_floats, p.chunks_per_tile, p.tm_agg >= 0, st[0], st[1], st[2]);
+                if ((size_t)sm.total <= budget) { found = sl; break; }
+            }
+            if (found) {
+                best_cps = cps;
+                best_slots = found;
+                best_epi = st[0];
+                best_f = st[1];
+                best_mst = st[2];
+                break;
+            }
         }
     }
     if (!best_cps) { *why = "no launch shape fits shared memory"; return TABNET_ERR_UNSUPPORTED_DIMS; }
     p.n_slots = best_slots;
     p.slot_bytes = slot_bytes;
-    p.sm = smem_layout(N, p.dp, d.n_feat, d.n_classes, d.n_d, best_slots, slot_bytes, split, nwg, p.epi_floats,
-                       best_epi, best_f);
+    p.sm = smem_layout(N, p.dp, d.d_emb, d.n_feat, d.n_classes, d.n_d, best_slots, slot_bytes, split, nwg,
+                       p.epi_floats, p.chunks_per_tile, p.tm_agg >= 0, best_epi, best_f, best_mst);
     size_t smem = (size_t)p.sm.total + 1024;
     // request enough shared memory that no more than best_cps CTAs share an SM
     const size_t floor_smem = (size_t)dev_smem_sm / (best_cps + 1) + 1;

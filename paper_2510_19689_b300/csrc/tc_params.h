@@ -13,11 +13,15 @@ struct TcSmem {
     int a_hi;   // A operand (activations, bf16, SW128 K-major, 16 KB per 64 K-columns)
     int a_lo;   // low halves of the split-bf16 A operand (-1 unless split)
     int ring;   // weight-staging ring: n_slots x slot_bytes
-    int agg;    // aggregate per original feature, float [d][128]
+    int agg;    // aggregate per original feature, float [d][128] (-1: kept in TMEM)
     int xch;    // cross-warpgroup exchange, float2 [2][2][128] (-1 with one warpgroup)
     int wf;     // final linear weights, float [n_classes][n_d]
     int epi;    // every layer's folded BN scale/shift (-1: read from global)
-    int fcache; // embedded, BN'd input of the tile, float [dp][128] (-1: recomputed)
+    int fcache; // embedded, BN'd input of the tile, float [de][129] (-1: recomputed)
+    int rowp;   // with fcache: the tile's row pointers, [128] x_num, [128] x_cat, [128] masks
+    int mstage; // one step's masks of the tile, float [de][129], written out row by row (-1: direct stores)
+    int chunks; // the weight-chunk table, uint2 [chunks_per_tile]
+    int colf;   // original feature of each embedded column, int [dp]
     int bar;    // mbarriers: n_slots full, n_slots empty, 1 accumulator; TMEM address; abort flag
     int total;  // bytes used (without the alignment slack)
 };
@@ -28,9 +32,10 @@ struct TcParams {
     const uint8_t* wbase;      // packed weight chunks (device)
     const uint2* chunks;       // [chunks_per_tile] {byte offset from wbase, bytes}, stream order
     int chunks_per_tile;
-    // Every layer's folded BN as one float block: feature-transformer layer
-    // L = s * layers_per_ft + l at L * 4N (scale[2N], shift[2N]), then the
-    // attentive layer of step i at n_ft_layers * 4N + i * 2 dp (scale[dp], shift[dp]).
+    // Every layer's BN shift (the scale is folded into the packed weights) as
+    // one float block: feature-transformer layer L = s * layers_per_ft + l at
+    // L * 2N (shift[2N]), then the attentive layer of step i at
+    // n_ft_layers * 2N + i * dp (shift[dp]).
     const float* epi;
     int epi_floats;
     const int2* col_info;      // [dp]: {-1, numeric column} | {categorical j, element e} | {-2, 0} pad
@@ -41,6 +46,7 @@ struct TcParams {
     int tmem_cols;             // TMEM columns allocated per CTA
     int tm_p;                  // TMEM column of the prior P (fp32, dp columns)
     int tm_m;                  // TMEM column of the current mask (fp16 pairs, dp/2 columns)
+    int tm_agg;                // TMEM column of the aggregate (fp32, dp columns; -1: in shared memory)
     int n_slots;
     int slot_bytes;
     TcSmem sm;
