@@ -260,6 +260,43 @@ def bench_batching(model, params, dev, stream, n_segs=4096, max_rows=4096, reps=
                                          "(prefix-sum scan + forward)"}
 
 
+def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), seconds=1.0):
+    """Poisson arrivals at each rate for `seconds`, request sizes
+    floor(exp(U(0, ln 513))) in [1, 512] rows, the three model shapes
+    resident (split-bf16), model chosen uniformly; the server's latency
+    (completion seen on the host - submission) and completed rows/s."""
+    import numpy as np
+    from paper_2510_19689_b300 import synth, tabnet
+    names = ["c1", "c2", "c3"]
+    models = [tabnet.Model(synth.to_blob(synth.make_params(synth.SPECS[n], synth.weight_seed(n))), "bf16x3",
+                           device=dev_index) for n in names]
+    pools = [synth.make_rows(n, 512, seed=5000 + i) for i, n in enumerate(names)]
+    srv = tabnet.Server(models, device_bytes=2 << 30)
+    out = []
+    for rate in rates:
+        rng = np.random.default_rng(rate)
+        n = int(rate * seconds)
+        t = np.cumsum(rng.exponential(1.0 / rate, n))
+        sizes = np.clip(np.floor(np.exp(rng.uniform(0, math.log(513), n))), 1, 512).astype(int)
+        which = rng.integers(0, 3, n)
+        reqs = [(int(which[k]), pools[which[k]][0][:sizes[k]], pools[which[k]][1][:sizes[k]], float(t[k]))
+                for k in range(n)]
+        srv.reset_stats()
+        t0 = time.perf_counter()
+        srv.replay(reqs)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        out.append({"offered_req_per_s": rate, "requests": n, "completed": st["completed"],
+                    "achieved_req_per_s": st["completed"] / wall, "rows_per_s": st["rows_completed"] / wall,
+                    "p50_ms": st["p50_ms"], "p95_ms": st["p95_ms"], "p99_ms": st["p99_ms"],
+                    "mean_batch_rows": st["mean_batch_rows"], "batches": st["batches"]})
+    srv.close()
+    for m in models:
+        m.close()
+    return {"models": "14-, 35- and 100-input models resident, split-bf16", "request_rows": "log-uniform 1..512",
+            "rates": out}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -429,6 +466,7 @@ def main():
 
     if rank == 0 and not args.no_extras and args.precision != "fp32" and name == "c2":
         extras["batching"] = bench_batching(model, params, dev, stream)
+        extras["serving"] = bench_serving(local)
 
     if rank == 0:
         line = {

@@ -231,6 +231,89 @@ int tabnet_set_tile_config(tabnet_model* model, int nwg, int n_slots, int ctas_p
  * UNSUPPORTED_DIMS for the fp32 precision. */
 int tabnet_get_tile_config(const tabnet_model* model, int* nwg, int* n_slots, int* ctas_per_sm);
 
+/* ---------------------------------------------------------------- serving
+ * A continuous-batching request server over resident models on one GPU (the
+ * paper's GPU functions keep the model in GPU memory and serve batches of
+ * records per invocation, Sec. III-B, judged by p50/p95/p99 latency,
+ * Sec. IV-C).  An engine thread owned by the server packs every request
+ * that has arrived for a model into one batch in that model's device ring
+ * (admission by device memory: a request waits while the ring is full), runs
+ * it as one forward launch with one copy in and one copy out on one of the
+ * model's streams, and forms the next batch without waiting, so requests
+ * arriving while others run are admitted as memory frees and overlap on the
+ * device.  Latency = completion observed on the host - submission. */
+typedef struct tabnet_server tabnet_server;
+
+typedef struct {
+    size_t device_bytes;       /* device memory for all rings (0: 1 GiB), split by bytes per row */
+    int max_batch_rows;        /* rows per batch at most (0: 65536) */
+    int max_inflight_batches;  /* batches per model running on the GPU at once (0: 8); finished
+                                  but unreleased results hold ring memory, not a slot */
+    int streams_per_model;     /* CUDA streams per model (0: 2) */
+} tabnet_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, rows_completed, batches;
+    double mean_batch_rows;
+    double p50_ms, p95_ms, p99_ms, mean_ms, max_ms;  /* latency of completed requests */
+    double rows_per_s;                               /* completed rows / time since reset */
+    int64_t queue_depth, inflight_batches;
+    size_t device_bytes_in_use;
+} tabnet_server_stats;
+
+/* One request of a replayed trace (tabnet_server_replay). */
+typedef struct {
+    int model;              /* index into the server's models */
+    const float* x_num;     /* host [rows, n_num] */
+    const int32_t* x_cat;   /* host [rows, n_cat] */
+    int64_t rows;
+    double arrival_s;       /* offset from the start of the replay */
+} tabnet_server_request;
+
+/* Create a server over n_models loaded handles (all on one device; the
+ * handles must outlive the server).  cfg may be NULL.  Allocates the device
+ * rings and their pinned host mirrors and starts the engine thread.
+ * Errors: ARG, OOM. */
+int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet_server_config* cfg,
+                         tabnet_server** out);
+
+/* Queue a request: host inputs [rows, n_num] / [rows, n_cat] of model
+ * `model`, which must stay valid until the request is complete.  Returns at
+ * once with a ticket.  A request larger than the model's whole ring is
+ * rejected by the engine (counted in stats.rejected; it never completes).
+ * Thread-safe.  Errors: ARG, OOM. */
+int tabnet_server_submit(tabnet_server* server, int model, const float* x_num, const int32_t* x_cat,
+                         int64_t rows, uint64_t* ticket);
+
+/* Tickets completed since the last poll (at most max_tickets).  Returns the
+ * engine's sticky error (TABNET_OK normally). */
+int tabnet_server_poll(tabnet_server* server, uint64_t* tickets, int max_tickets, int* n_done);
+
+/* Block until the request is complete or timeout_s passes (TIMEOUT). */
+int tabnet_server_wait(tabnet_server* server, uint64_t ticket, double timeout_s);
+
+/* Pointers to a completed request's outputs (pinned host memory owned by the
+ * server, laid out as in tabnet_forward), valid until it is released. */
+int tabnet_server_result(tabnet_server* server, uint64_t ticket, const float** logits,
+                         const float** step_masks, const float** agg_mask, int64_t* rows);
+
+/* Give a completed request's result memory back (ring space is reused once
+ * every request of its batch and of older batches is released). */
+int tabnet_server_release(tabnet_server* server, uint64_t ticket);
+
+/* Counters and latency percentiles since the last reset. */
+int tabnet_server_get_stats(tabnet_server* server, tabnet_server_stats* stats);
+int tabnet_server_reset_stats(tabnet_server* server);
+
+/* Load driver: submit reqs[i] at its arrival offset (busy-waiting on the
+ * host clock) from the calling thread; with `release` != 0 completed
+ * requests are released as they finish and the call returns when all are
+ * done.  Errors: as tabnet_server_submit. */
+int tabnet_server_replay(tabnet_server* server, const tabnet_server_request* reqs, int n, int release);
+
+/* Stop the engine, wait for the GPU, free everything. */
+void tabnet_server_destroy(tabnet_server* server);
+
 /* Read and clear the handle's device status word (TABNET_STATUS_* bits) after
  * synchronising `stream`.  *status receives the bits; returns TABNET_OK when
  * no bit was set, TABNET_ERR_TIMEOUT when the timeout bit was set, else

@@ -35,6 +35,9 @@ EXPORTS = (
     "tabnet_destroy", "tabnet_status_string", "tabnet_last_error", "tabnet_set_tile_config",
     "tabnet_get_tile_config", "tabnet_forward_segments", "tabnet_forward_segments_device",
     "tabnet_reserve_segments", "tabnet_forward_segments_noalloc",
+    "tabnet_server_create", "tabnet_server_submit", "tabnet_server_poll", "tabnet_server_wait",
+    "tabnet_server_result", "tabnet_server_release", "tabnet_server_get_stats", "tabnet_server_reset_stats",
+    "tabnet_server_replay", "tabnet_server_destroy",
 )
 #: fixed scratch capacity of tabnet_forward_segments_noalloc
 NOALLOC_MAX_SEGMENTS = 65536
@@ -62,6 +65,28 @@ def segment_array(segs):
         arr[i] = Segment(_ptr(g.get("x_num")), _ptr(g.get("x_cat")), int(g["rows"]), _ptr(g.get("logits")),
                          _ptr(g.get("masks")), _ptr(g.get("agg")))
     return arr
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_size_t), ("max_batch_rows", ctypes.c_int),
+                ("max_inflight_batches", ctypes.c_int), ("streams_per_model", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("rows_completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("mean_batch_rows", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p95_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("rows_per_s", ctypes.c_double), ("queue_depth", ctypes.c_int64),
+                ("inflight_batches", ctypes.c_int64), ("device_bytes_in_use", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerRequest(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("x_num", ctypes.c_void_p), ("x_cat", ctypes.c_void_p),
+                ("rows", ctypes.c_int64), ("arrival_s", ctypes.c_double)]
 
 
 class Dims(ctypes.Structure):
@@ -104,6 +129,18 @@ def lib() -> ctypes.CDLL:
     L.tabnet_forward_segments_device.argtypes = [vp, vp, i32, vp]
     L.tabnet_reserve_segments.argtypes = [vp, i32]
     L.tabnet_forward_segments_noalloc.argtypes = [vp, vp, i32, vp]
+    L.tabnet_server_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    L.tabnet_server_submit.argtypes = [vp, i32, vp, vp, i64, ctypes.POINTER(ctypes.c_uint64)]
+    L.tabnet_server_poll.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), i32, ctypes.POINTER(ctypes.c_int)]
+    L.tabnet_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double]
+    fpp = ctypes.POINTER(ctypes.POINTER(ctypes.c_float))
+    L.tabnet_server_result.argtypes = [vp, ctypes.c_uint64, fpp, fpp, fpp, ctypes.POINTER(ctypes.c_int64)]
+    L.tabnet_server_release.argtypes = [vp, ctypes.c_uint64]
+    L.tabnet_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    L.tabnet_server_reset_stats.argtypes = [vp]
+    L.tabnet_server_replay.argtypes = [vp, ctypes.POINTER(ServerRequest), i32, i32]
+    L.tabnet_server_destroy.argtypes = [vp]
+    L.tabnet_server_destroy.restype = None
     L.tabnet_destroy.argtypes = [vp]
     L.tabnet_destroy.restype = None
     L.tabnet_status_string.argtypes = [i32]
@@ -113,7 +150,9 @@ def lib() -> ctypes.CDLL:
                  "tabnet_forward", "tabnet_forward_host", "tabnet_poll_status",
                  "tabnet_set_tile_config", "tabnet_get_tile_config", "tabnet_forward_segments",
                  "tabnet_forward_segments_device", "tabnet_reserve_segments",
-                 "tabnet_forward_segments_noalloc"):
+                 "tabnet_forward_segments_noalloc", "tabnet_server_create", "tabnet_server_submit",
+                 "tabnet_server_poll", "tabnet_server_wait", "tabnet_server_result", "tabnet_server_release",
+                 "tabnet_server_get_stats", "tabnet_server_reset_stats", "tabnet_server_replay"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -239,6 +278,92 @@ class Model:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().tabnet_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server over resident models
+    (tabnet_server_*).  Inputs are numpy arrays kept alive until release."""
+
+    def __init__(self, models, device_bytes=1 << 30, max_batch_rows=65536, max_inflight_batches=8,
+                 streams_per_model=2):
+        self.models = list(models)
+        arr = (ctypes.c_void_p * len(self.models))(*[m.handle for m in self.models])
+        cfg = ServerConfig(device_bytes, max_batch_rows, max_inflight_batches, streams_per_model)
+        h = ctypes.c_void_p()
+        _check(lib().tabnet_server_create(arr, len(self.models), ctypes.byref(cfg), ctypes.byref(h)),
+               "tabnet_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, model: int, x_num: np.ndarray, x_cat: np.ndarray) -> int:
+        d = self.models[model].dims
+        rows = x_num.shape[0] if d.n_num else x_cat.shape[0]
+        x_num = np.ascontiguousarray(x_num, dtype=np.float32)
+        x_cat = np.ascontiguousarray(x_cat, dtype=np.int32)
+        t = ctypes.c_uint64()
+        _check(lib().tabnet_server_submit(self._h, model, _ptr(x_num) if d.n_num else None,
+                                          _ptr(x_cat) if d.n_cat else None, rows, ctypes.byref(t)),
+               "tabnet_server_submit")
+        self._keep[t.value] = (x_num, x_cat, model, rows)
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 30.0) -> None:
+        _check(lib().tabnet_server_wait(self._h, ticket, timeout_s), "tabnet_server_wait")
+
+    def result(self, ticket: int):
+        """Copies of (logits, step_masks, agg_mask) of a completed request."""
+        _, _, model, rows = self._keep[ticket]
+        d = self.models[model].dims
+        pl, pm, pa = (ctypes.POINTER(ctypes.c_float)() for _ in range(3))
+        r = ctypes.c_int64()
+        _check(lib().tabnet_server_result(self._h, ticket, ctypes.byref(pl), ctypes.byref(pm), ctypes.byref(pa),
+                                          ctypes.byref(r)), "tabnet_server_result")
+        lg = np.ctypeslib.as_array(pl, shape=(rows, d.n_classes)).copy()
+        mk = np.ctypeslib.as_array(pm, shape=(rows, d.n_steps, d.d_emb)).copy()
+        ag = np.ctypeslib.as_array(pa, shape=(rows, d.n_feat)).copy()
+        return lg, mk, ag
+
+    def release(self, ticket: int) -> None:
+        _check(lib().tabnet_server_release(self._h, ticket), "tabnet_server_release")
+        self._keep.pop(ticket, None)
+
+    def poll(self, max_tickets: int = 4096):
+        buf = (ctypes.c_uint64 * max_tickets)()
+        n = ctypes.c_int()
+        _check(lib().tabnet_server_poll(self._h, buf, max_tickets, ctypes.byref(n)), "tabnet_server_poll")
+        return list(buf[:n.value])
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().tabnet_server_get_stats(self._h, ctypes.byref(st)), "tabnet_server_get_stats")
+        return st.as_dict()
+
+    def reset_stats(self) -> None:
+        _check(lib().tabnet_server_reset_stats(self._h), "tabnet_server_reset_stats")
+
+    def replay(self, requests, release: bool = True) -> None:
+        """requests: list of (model, x_num, x_cat, arrival_s) with numpy inputs."""
+        arr = (ServerRequest * len(requests))()
+        keep = []
+        for i, (model, xn, xc, t) in enumerate(requests):
+            xn = np.ascontiguousarray(xn, dtype=np.float32)
+            xc = np.ascontiguousarray(xc, dtype=np.int32)
+            keep.append((xn, xc))
+            d = self.models[model].dims
+            rows = xn.shape[0] if d.n_num else xc.shape[0]
+            arr[i] = ServerRequest(model, _ptr(xn) if d.n_num else None, _ptr(xc) if d.n_cat else None, rows, t)
+        _check(lib().tabnet_server_replay(self._h, arr, len(requests), 1 if release else 0), "tabnet_server_replay")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tabnet_server_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

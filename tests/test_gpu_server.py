@@ -1,0 +1,124 @@
+"""The continuous-batching server (tabnet_server_*) on the GPU.
+
+The paper's GPU functions keep the model resident and answer batches of
+records with predictions and attribution masks (Sec. III-B); here many
+requests of three resident models are served at once.  A request's result
+must be the same alone and in a mix (rows are independent), and admission by
+device memory must hold requests back rather than fail them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import tabnet_oracle as O
+from paper_2510_19689_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NAMES = ["c1", "c2", "c3"]
+
+
+@pytest.fixture(scope="module")
+def models():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_19689_b300 import tabnet
+    params = [synth.make_params(synth.SPECS[n], 70 + i, bn_affine="random") for i, n in enumerate(NAMES)]
+    ms = [tabnet.Model(synth.to_blob(p), "bf16x3") for p in params]
+    yield tabnet, params, ms
+    for m in ms:
+        m.close()
+
+
+def _req(name, rows, seed):
+    return synth.make_rows(name, rows, seed=seed)
+
+
+def test_same_result_alone_and_in_a_mix(models):
+    tabnet, params, ms = models
+    srv = tabnet.Server(ms, device_bytes=256 << 20)
+    targets = [(i, *_req(n, r, 100 + i)) for i, (n, r) in enumerate(zip(NAMES, [37, 300, 129]))]
+    alone = []
+    for i, xn, xc in targets:
+        t = srv.submit(i, xn, xc)
+        srv.wait(t)
+        alone.append(srv.result(t))
+        srv.release(t)
+    # the same requests again, each in the middle of a burst of other requests
+    rng = np.random.default_rng(5)
+    tickets, mine = [], {}
+    for k in range(300):
+        i = int(rng.integers(3))
+        xn, xc = _req(NAMES[i], int(rng.integers(1, 200)), 1000 + k)
+        tickets.append(srv.submit(i, xn, xc))
+        if k in (100, 150, 200):
+            j = (100, 150, 200).index(k)
+            mine[j] = srv.submit(targets[j][0], targets[j][1], targets[j][2])
+    for j, t in mine.items():
+        srv.wait(t)
+        for a, b in zip(alone[j], srv.result(t)):
+            np.testing.assert_array_equal(a, b)
+        srv.release(t)
+    for t in tickets:
+        srv.wait(t)
+        srv.release(t)
+    st = srv.stats()
+    assert st["rejected"] == 0 and st["completed"] == st["submitted"]
+    assert st["batches"] < st["submitted"]  # requests were batched together
+    srv.close()
+    # and against the oracle (split-bf16 bar)
+    for (i, xn, xc), (lg, mk, ag) in zip(targets, alone):
+        rl, rm, ra = O.forward(params[i], xn, xc)
+        assert np.abs(lg - rl).max() <= 2e-2
+        assert np.abs(mk - rm).sum(axis=(1, 2)).max() <= 2e-2
+        assert np.abs(ag - ra).sum(axis=1).max() <= 2e-2
+
+
+def test_admission_waits_for_memory(models):
+    tabnet, params, ms = models
+    # rings sized for only a few hundred rows of the 100-input model
+    srv = tabnet.Server(ms, device_bytes=8 << 20, max_batch_rows=512)
+    tickets = []
+    for k in range(60):
+        i = k % 3
+        xn, xc = _req(NAMES[i], 200, 2000 + k)
+        tickets.append(srv.submit(i, xn, xc))
+    for t in tickets:
+        srv.wait(t, 60.0)
+        srv.release(t)
+    st = srv.stats()
+    assert st["completed"] == 60 and st["rejected"] == 0
+    # a request larger than its model's whole ring is rejected, not hung
+    xn, xc = _req("c3", 4000, 3000)
+    srv.submit(2, xn, xc)
+    for _ in range(200):
+        if srv.stats()["rejected"] == 1:
+            break
+        import time
+        time.sleep(0.01)
+    assert srv.stats()["rejected"] == 1
+    srv.close()
+
+
+def test_poisson_replay(models):
+    tabnet, params, ms = models
+    srv = tabnet.Server(ms, device_bytes=512 << 20)
+    rng = np.random.default_rng(9)
+    pools = [_req(n, 512, 4000 + i) for i, n in enumerate(NAMES)]
+    n_req, rate = 3000, 20000.0
+    t = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    sizes = np.minimum(512, np.floor(np.exp(rng.uniform(0, math.log(513), n_req)))).astype(int)
+    reqs = []
+    for k in range(n_req):
+        i = int(rng.integers(3))
+        xn, xc = pools[i]
+        reqs.append((i, xn[:sizes[k]], xc[:sizes[k]], float(t[k])))
+    srv.reset_stats()
+    srv.replay(reqs)
+    st = srv.stats()
+    assert st["completed"] == n_req and st["rejected"] == 0
+    assert st["rows_completed"] == int(sizes.sum())
+    assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
+    srv.close()
