@@ -33,6 +33,7 @@ struct TcLaunch {
     int ctas_per_sm = 1;  // resident CTAs per SM
     size_t smem = 0;      // dynamic shared memory per CTA
     bool zreg = false;    // sparsemax input held in registers
+    bool lean = false;    // everything staged: the specialised kernel instantiation
 };
 
 }  // namespace tabnet

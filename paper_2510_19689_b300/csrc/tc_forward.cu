@@ -55,7 +55,7 @@ namespace {
 
 constexpr uint64_t kWaitLimit = 1000000000ull;  // 1 s per wait
 constexpr float kSqrtHalf = 0.70710678118654752440f;
-constexpr int kMaxClasses = 8;
+constexpr int kMaxClasses = 4;
 constexpr int kFStride = 129;  // row stride (floats) of the input cache: transposed writes hit distinct banks
 // sparsemax input kept in registers: up to this many 16-column chunks per thread
 __host__ __device__ constexpr int zreg_chunks(int nwg) { return nwg == 1 ? 3 : 2; }
@@ -105,10 +105,11 @@ __device__ __forceinline__ void note_timeout(unsigned* status, unsigned kind, un
 }
 
 // sigmoid(x) = 1 / (1 + 2^(-x log2 e)) with the ex2/rcp approximations
-// (about 2^-21 relative): the split mode's gate.
-__device__ __forceinline__ float sigmoid_accurate(float x) {
+// (about 2^-21 relative): the split mode's gate.  The argument is y =
+// -x log2 e, already scaled by the packed gate weights and shifts.
+__device__ __forceinline__ float sigmoid_from_log2(float y) {
     float e, r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x * -1.4426950408889634f));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
     return r;
 }
@@ -156,12 +157,16 @@ __device__ __forceinline__ void store_a16(uint8_t* sA, uint8_t* sAlo, int r, int
 
 // Folded-BN vectors: staged in shared memory (epi_s != 0, a shared address)
 // or read through the read-only path from global memory.
+template <bool STAGED>
 __device__ __forceinline__ float4 ld_epi(const float* g, uint32_t epi_s, int idx) {
-    if (epi_s) return ptx::ld_shared_f4(epi_s + 4u * (uint32_t)idx);
+    if (STAGED || epi_s) return ptx::ld_shared_f4(epi_s + 4u * (uint32_t)idx);
     return __ldg(reinterpret_cast<const float4*>(g + idx));
 }
 
-template <int N, int NWG, bool SPLIT, bool ZREG>
+// LEAN: the launch shape stages the BN shifts, the input cache and the mask
+// stage in shared memory and keeps the aggregate in TMEM, so the kernel is
+// compiled with only those paths (smaller code, fewer instruction misses).
+template <int N, int NWG, bool SPLIT, bool ZREG, bool LEAN>
 __global__ void __launch_bounds__(128 * NWG, (NWG == 2 && N <= 64) ? 2 : 1)
 tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* __restrict__ x_cat,
                   int64_t rows, float* __restrict__ logits, float* __restrict__ masks,
@@ -184,8 +189,10 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     float* sAgg = reinterpret_cast<float*>(smem + (p.sm.agg >= 0 ? p.sm.agg : 0));
     float2* sX = reinterpret_cast<float2*>(smem + (p.sm.xch >= 0 ? p.sm.xch : 0));
     float* sWf = reinterpret_cast<float*>(smem + p.sm.wf);
-    const uint32_t f_s = p.sm.fcache >= 0 ? ptx::smem_u32(smem + p.sm.fcache) : 0u;  // f cache (shared address)
-    const uint32_t epi_s = p.sm.epi >= 0 ? ptx::smem_u32(smem + p.sm.epi) : 0u;      // BN vectors (shared address)
+    const uint32_t wf_s = ptx::smem_u32(sWf);
+    const bool has_f = LEAN || p.sm.fcache >= 0;
+    const uint32_t f_s = has_f ? ptx::smem_u32(smem + p.sm.fcache) : 0u;  // f cache (shared address)
+    const uint32_t epi_s = (LEAN || p.sm.epi >= 0) ? ptx::smem_u32(smem + p.sm.epi) : 0u;  // BN vectors
     const float* epi = p.epi;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.sm.bar);
     const int S = p.n_slots;
@@ -212,7 +219,10 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     for (int i = tid; i < p.dp; i += THREADS) sColf[i] = __ldg(p.col_feat + i);
     uint2* sChunks = reinterpret_cast<uint2*>(smem + p.sm.chunks);
     for (int i = tid; i < p.chunks_per_tile; i += THREADS) sChunks[i] = __ldg(p.chunks + i);
-    for (int i = tid; i < m.n_classes * m.n_d; i += THREADS) sWf[i] = __ldg(m.wf + i);
+    for (int i = tid; i < m.n_classes * N; i += THREADS) {
+        const int k = i / N, c = i % N;
+        sWf[i] = c < m.n_d ? __ldg(m.wf + k * m.n_d + c) : 0.f;
+    }
     if (p.sm.epi >= 0)
         for (int i = tid; i < p.epi_floats / 4; i += THREADS)
             reinterpret_cast<float4*>(smem + p.sm.epi)[i] = __ldg(reinterpret_cast<const float4*>(p.epi) + i);
@@ -225,7 +235,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     const uint32_t t_acc = tmem + lane_off;
     const uint32_t t_p = t_acc + (uint32_t)p.tm_p;
     const uint32_t t_m = t_acc + (uint32_t)p.tm_m;
-    const bool agg_tmem = p.tm_agg >= 0;
+    const bool agg_tmem = LEAN || p.tm_agg >= 0;
     const uint32_t t_agg = t_acc + (uint32_t)(agg_tmem ? p.tm_agg : 0);
 
     const int64_t total = total_rows(p.seg, rows);
@@ -279,6 +289,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             ptx::tc_fence_after();
             int kk = 0;
             bool ok = true;
+#pragma unroll 1
             for (int b = 0; b < kblocks && ok; ++b) {
                 while (ok && g_issue < g_cons + PARTS) ok = issue_next();
                 // slots (and rounds) of this K block's hi and lo chunks
@@ -404,8 +415,8 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         };
 
         // ---- tile start: f -> A (K = dp), P = 1, aggregate = 0
-        float* fc = reinterpret_cast<float*>(smem + (f_s ? p.sm.fcache : 0));
-        if (f_s) {
+        float* fc = reinterpret_cast<float*>(smem + (has_f ? p.sm.fcache : 0));
+        if (has_f) {
             // Gather the tile's inputs cooperatively: warp w takes 128/(4 NWG)
             // rows, its lanes walk the columns (coalesced reads of a row),
             // all rows' loads in flight before any use.
@@ -420,50 +431,61 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             }
             __syncthreads();
             const int lane = tid & 31, r0 = warp * RPW;
+            constexpr int G = 8;  // rows whose loads are in flight together
+#pragma unroll 1
             for (int cb = 0; cb < m.n_num; cb += 32) {
                 const int c = cb + lane;
-                float xv[RPW];
-#pragma unroll
-                for (int i = 0; i < RPW; ++i) {
-                    const float* xr = sRowX[r0 + i];
-                    xv[i] = (c < m.n_num && xr) ? __ldg(xr + c) : 0.f;
-                }
                 if (c < m.n_num) {
                     const float s0 = __ldg(m.s0 + c), t0 = __ldg(m.t0 + c);
+#pragma unroll 1
+                    for (int i0 = r0; i0 < r0 + RPW; i0 += G) {
+                        float xv[G];
 #pragma unroll
-                    for (int i = 0; i < RPW; ++i) fc[c * kFStride + r0 + i] = fmaf(s0, xv[i], t0);
+                        for (int i = 0; i < G; ++i) {
+                            const float* xr = sRowX[i0 + i];
+                            xv[i] = xr ? __ldg(xr + c) : 0.f;
+                        }
+#pragma unroll
+                        for (int i = 0; i < G; ++i) fc[c * kFStride + i0 + i] = fmaf(s0, xv[i], t0);
+                    }
                 }
             }
+#pragma unroll 1
             for (int jb = 0; jb < m.n_cat; jb += 32) {
                 const int j = jb + lane;
-                int iv[RPW];
-#pragma unroll
-                for (int i = 0; i < RPW; ++i) {
-                    const int* cr = sRowC[r0 + i];
-                    iv[i] = (j < m.n_cat && cr) ? __ldg(cr + j) : 0;
-                }
                 if (j < m.n_cat) {
                     const int card = __ldg(m.cat_card + j);
                     const int c0 = __ldg(m.feat_col + m.n_num + j), len = __ldg(m.feat_len + m.n_num + j);
                     const float* tab = m.emb + __ldg(m.cat_off + j);
+#pragma unroll 1
+                    for (int i0 = r0; i0 < r0 + RPW; i0 += G) {
+                        int iv[G];
 #pragma unroll
-                    for (int i = 0; i < RPW; ++i) {
-                        const bool oob = iv[i] < 0 || iv[i] >= card;
-                        if (oob && sRowC[r0 + i]) atomicOr(m.status, TABNET_STATUS_CAT_OOB);
-                        for (int e = 0; e < len; ++e)
-                            fc[(c0 + e) * kFStride + r0 + i] =
-                                oob ? __ldg(m.t0 + c0 + e) : __ldg(tab + (size_t)iv[i] * len + e);
+                        for (int i = 0; i < G; ++i) {
+                            const int* cr = sRowC[i0 + i];
+                            iv[i] = cr ? __ldg(cr + j) : 0;
+                        }
+#pragma unroll 1
+                        for (int i = 0; i < G; ++i) {
+                            const bool oob = iv[i] < 0 || iv[i] >= card;
+                            if (oob && sRowC[i0 + i]) atomicOr(m.status, TABNET_STATUS_CAT_OOB);
+#pragma unroll 1
+                            for (int e = 0; e < len; ++e)
+                                fc[(c0 + e) * kFStride + i0 + i] =
+                                    oob ? __ldg(m.t0 + c0 + e) : __ldg(tab + (size_t)iv[i] * len + e);
+                        }
                     }
                 }
             }
             __syncthreads();
         }
+#pragma unroll 1
         for (int ch = wg; ch < dch; ch += NWG) {
             float v[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int c = ch * 16 + j;
-                v[j] = f_s ? (c < de ? fc[c * kFStride + lt] : 0.f) : f_value(c, valid);
+                v[j] = has_f ? (c < de ? fc[c * kFStride + lt] : 0.f) : f_value(c, valid);
             }
             store_a16<SPLIT>(sA, sAlo, lt, ch, v);
             uint32_t ones[16];
@@ -498,7 +520,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     ptx::tmem_wait_ld(acc, pr);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 b = ld_epi(epi, epi_s, ash + ch * 16 + 4 * q);
+                        const float4 b = ld_epi<LEAN>(epi, epi_s, ash + ch * 16 + 4 * q);
                         const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
                         for (int t = 0; t < 4; ++t) {
@@ -541,6 +563,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 // loads and the warpgroup exchange are collective: every thread
                 // runs every pass until the last row of its warp (CTA) has
                 // converged; a converged row keeps its threshold.
+#pragma unroll 1
                 for (int it = 0; it < de; ++it) {
                     float ss = 0.f, cnt = 0.f;
                     if constexpr (ZREG) {
@@ -582,7 +605,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 PH_MARK(2);
                 // Mask, prior, masked input (A for the step's first FC), outputs.
                 float* mrow = (io.masks && valid) ? io.masks + (size_t)(s - 1) * de : nullptr;
-                float* mst = p.sm.mstage >= 0 ? reinterpret_cast<float*>(smem + p.sm.mstage) : nullptr;
+                float* mst = (LEAN || p.sm.mstage >= 0) ? reinterpret_cast<float*>(smem + p.sm.mstage) : nullptr;
 #pragma unroll 1
                 for (int il = 0; wg + il * NWG < dch; ++il) {
                     const int ch = wg + il * NWG;
@@ -619,7 +642,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int c = ch * 16 + j;
-                        if (f_s) {
+                        if (has_f) {
                             v[j] = c < de ? mk[j] * ptx::ld_shared_f32(f_s + 4u * (uint32_t)(c * kFStride + lt)) : 0.f;
                         } else {
                             v[j] = (c < de && mk[j] > 0.f) ? mk[j] * f_value(c, false) : 0.f;
@@ -651,11 +674,13 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     constexpr int RPW = 128 / (4 * NWG);
                     float** sRowM = reinterpret_cast<float**>(smem + p.sm.rowp + 128 * 16);
                     const int lane = tid & 31;
+#pragma unroll 1
                     for (int i = 0; i < RPW; ++i) {
                         const int r = warp * RPW + i;
                         float* dst = sRowM[r];
                         if (dst) {
                             dst += (size_t)(s - 1) * de;
+#pragma unroll 1
                             for (int c = lane; c < de; c += 32) dst[c] = mst[c * kFStride + r];
                         }
                     }
@@ -664,6 +689,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             }
 
             // ---- feature transformer s
+#pragma unroll 1
             for (int l = 0; l < lpf; ++l) {
                 const bool first = (l == 0);
                 if (!run_mma(first ? p.k0_blocks : p.kn_blocks, first ? dch : N / 16, idesc_ft)) {
@@ -678,6 +704,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 ptx::tmem_ld16(t_acc + wg * CPW, lin[0]);
                 ptx::tmem_ld16(t_acc + N + wg * CPW, gat[0]);
                 ptx::tmem_wait_ld(lin[0], gat[0]);
+                PH_MARK(14);
 #pragma unroll
                 for (int cc = 0; cc < RCH; ++cc) {
                     const int c0 = wg * CPW + cc * 16;
@@ -689,8 +716,8 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     float4 hl4[4], hg4[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        hl4[q] = ld_epi(epi, epi_s, sh + c0 + 4 * q);
-                        hg4[q] = ld_epi(epi, epi_s, sh + N + c0 + 4 * q);
+                        hl4[q] = ld_epi<LEAN>(epi, epi_s, sh + c0 + 4 * q);
+                        hg4[q] = ld_epi<LEAN>(epi, epi_s, sh + N + c0 + 4 * q);
                     }
                     float out[16];
 #pragma unroll
@@ -702,7 +729,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                             const int j = 4 * q + t;
                             const float ul = __uint_as_float(lin[cur][j]) + hlv[t];
                             const float ug = __uint_as_float(gat[cur][j]) + hgv[t];
-                            const float g = ul * (SPLIT ? sigmoid_accurate(ug) : sigmoid_fast(ug));
+                            const float g = ul * (SPLIT ? sigmoid_from_log2(ug) : sigmoid_fast(ug));
                             const float x = first ? g : (res[cc][j] + g) * kSqrtHalf;
                             res[cc][j] = x;
                             out[j] = x;
@@ -717,25 +744,42 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 
             if (s > 0) {
                 // ---- decision output: acc += ReLU(d) (folded into the logits), eta, aggregate
+                // res becomes ReLU(d) (zero on the attention columns): the next
+                // step's feature transformer starts from its own first layer.
                 float eta = 0.f;
 #pragma unroll
                 for (int cc = 0; cc < RCH; ++cc) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int c = wg * CPW + cc * 16 + j;
-                        if (c < n_d) {
-                            const float dv = fmaxf(res[cc][j], 0.f);
-                            eta += dv;
+                        const float dv = c < n_d ? fmaxf(res[cc][j], 0.f) : 0.f;
+                        res[cc][j] = dv;
+                        eta += dv;
+                    }
+                }
+                // logits += W_f ReLU(d), W_f staged as [class][N] with zero columns past n_d
 #pragma unroll
-                            for (int k = 0; k < kMaxClasses; ++k) {
-                                if (k >= n_cls) break;
-                                lacc[k] = fmaf(sWf[k * n_d + c], dv, lacc[k]);
+                for (int k = 0; k < kMaxClasses; ++k) {
+                    if (k < n_cls) {
+                        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                        for (int cc = 0; cc < RCH; ++cc) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const float4 w = ptx::ld_shared_f4(wf_s + 4u * (uint32_t)(k * N + wg * CPW + cc * 16 + 4 * q));
+                                a0 = fmaf(w.x, res[cc][4 * q], a0);
+                                a1 = fmaf(w.y, res[cc][4 * q + 1], a1);
+                                a0 = fmaf(w.z, res[cc][4 * q + 2], a0);
+                                a1 = fmaf(w.w, res[cc][4 * q + 3], a1);
                             }
                         }
+                        lacc[k] += a0 + a1;
                     }
                 }
                 eta = xsum(eta, 0.f).x;
+                PH_MARK(5);
                 if (agg_tmem) {
+#pragma unroll 1
                     for (int ch = wg; ch < dch; ch += NWG) {
                         uint32_t mh[8], ag[16];
                         ptx::tmem_ld8(t_m + ch * 8, mh);
@@ -752,6 +796,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                         ptx::tmem_st16(t_agg + ch * 16, ag);
                     }
                     ptx::tmem_wait_st();
+                    PH_MARK(15);
                 } else
                 for (int ch = wg; ch < dch; ch += NWG) {
                     uint32_t mh[8];
@@ -788,6 +833,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         if (agg_tmem) {
             // one column per feature: normalise the TMEM aggregate directly
             float tot = 0.f;
+#pragma unroll 1
             for (int ch = wg; ch < dch; ch += NWG) {
                 uint32_t ag[16];
                 ptx::tmem_ld16(t_agg + ch * 16, ag);
@@ -798,6 +844,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             }
             tot = xsum(tot, 0.f).x;
             const float inv = tot > 0.f ? 1.f / tot : 0.f;
+#pragma unroll 1
             for (int ch = wg; ch < dch; ch += NWG) {
                 uint32_t ag[16];
                 ptx::tmem_ld16(t_agg + ch * 16, ag);
@@ -887,22 +934,24 @@ int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
 struct Variant {
     int N, nwg;
-    bool split, zreg;
+    bool split, zreg, lean;
 };
 
 // Run f on the kernel instantiation of a variant; false when none exists.
 template <typename F>
 bool with_kernel(const Variant& v, F&& f) {
-#define TC_VARIANT(NN, WW)                                                  \
-    if (v.N == NN && v.nwg == WW) {                                         \
-        if (v.split) {                                                      \
-            if (v.zreg) f(tc_forward_kernel<NN, WW, true, true>);            \
-            else f(tc_forward_kernel<NN, WW, true, false>);                  \
-        } else {                                                            \
-            if (v.zreg) f(tc_forward_kernel<NN, WW, false, true>);           \
-            else f(tc_forward_kernel<NN, WW, false, false>);                 \
-        }                                                                   \
-        return true;                                                        \
+#define TC_VAR4(NN, WW, SP, ZR)                                                      \
+    if (v.split == SP && v.zreg == ZR) {                                             \
+        if (v.lean) f(tc_forward_kernel<NN, WW, SP, ZR, true>);                       \
+        else f(tc_forward_kernel<NN, WW, SP, ZR, false>);                            \
+        return true;                                                                 \
+    }
+#define TC_VARIANT(NN, WW)              \
+    if (v.N == NN && v.nwg == WW) {     \
+        TC_VAR4(NN, WW, true, true)     \
+        TC_VAR4(NN, WW, true, false)    \
+        TC_VAR4(NN, WW, false, true)    \
+        TC_VAR4(NN, WW, false, false)   \
     }
     TC_VARIANT(16, 1)
     TC_VARIANT(32, 1)
@@ -911,6 +960,7 @@ bool with_kernel(const Variant& v, F&& f) {
     TC_VARIANT(64, 2)
     TC_VARIANT(128, 2)
 #undef TC_VARIANT
+#undef TC_VAR4
     return false;
 }
 
@@ -927,7 +977,7 @@ TcSmem smem_layout(int N, int dp, int de, int d, int n_cls, int n_d, int n_slots
     if (!agg_tmem) { s.agg = o; o += round_up(d * 128 * 4, 16); }
     s.xch = -1;
     if (nwg > 1) { s.xch = o; o += 2 * 2 * 128 * 8; }
-    s.wf = o; o += round_up(n_cls * n_d * 4, 16);
+    s.wf = o; o += round_up(n_cls * N * 4, 16);
     s.epi = -1;
     if (with_epi) { s.epi = o; o += round_up(epi_floats * 4, 16); }
     s.fcache = -1;
@@ -961,7 +1011,7 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
         return TABNET_ERR_UNSUPPORTED_DIMS;
     }
     if (dp > 256) { *why = "tensor-core path needs d_emb <= 256"; return TABNET_ERR_UNSUPPORTED_DIMS; }
-    if (d.n_classes > kMaxClasses) { *why = "tensor-core path needs n_classes <= 8"; return TABNET_ERR_UNSUPPORTED_DIMS; }
+    if (d.n_classes > kMaxClasses) { *why = "tensor-core path needs n_classes <= 4"; return TABNET_ERR_UNSUPPORTED_DIMS; }
     const int accw = std::max(2 * N, dp);
     const int need = accw + dp + dp / 2;
     int cols = 32;
@@ -1027,6 +1077,13 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
             GluLayer g = hm.layer(s, l);
             std::vector<float> sc, sh;
             fold_bn(*g.bn, d.bn_eps, sc, sh);
+            if (split) {
+                // gate half pre-scaled by -log2(e): the kernel's sigmoid takes 2^(-x log2 e) directly
+                for (int n = N; n < 2 * N; ++n) {
+                    sc[n] = (float)((double)sc[n] * -1.4426950408889634);
+                    sh[n] = (float)((double)sh[n] * -1.4426950408889634);
+                }
+            }
             const std::vector<float> ws = scaled(*g.w, sc, 2 * N, g.k);
             push_layer(ws.data(), 2 * N, g.k, 0, l == 0 ? dp : N, &stream);
             epi.insert(epi.end(), sh.begin(), sh.end());
@@ -1067,13 +1124,17 @@ int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std
     if (nwg != 1 && nwg != 2) { *why = "one or two warpgroups"; return TABNET_ERR_UNSUPPORTED_DIMS; }
     const int dch = p.dp / 16;
     const bool zreg = (dch + nwg - 1) / nwg <= zreg_chunks(nwg);
-    const Variant v{N, nwg, split, zreg};
-    cudaFuncAttributes fa{};
+    Variant v{N, nwg, split, zreg, false};
+    cudaFuncAttributes fa{}, fa_lean{};
     if (!with_kernel(v, [&](auto fn) { cudaFuncGetAttributes(&fa, fn); })) {
         *why = "no kernel for this shape";
         return TABNET_ERR_UNSUPPORTED_DIMS;
     }
-    const int regs = std::max(fa.numRegs, 1);
+    v.lean = true;
+    with_kernel(v, [&](auto fn) { cudaFuncGetAttributes(&fa_lean, fn); });
+    v.lean = false;
+    // either instantiation may run: size the CTA count for the larger register file
+    const int regs = std::max({fa.numRegs, fa_lean.numRegs, 1});
     int dev_smem_sm = 0;
     cudaDeviceGetAttribute(&dev_smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, m->device);
     const int reserved = 1024;
@@ -1125,6 +1186,8 @@ int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std
     m->tc_launch_cfg.ctas_per_sm = best_cps;
     m->tc_launch_cfg.smem = smem;
     m->tc_launch_cfg.zreg = zreg;
+    m->tc_launch_cfg.lean = p.tm_agg >= 0 && best_epi && best_f && best_mst;
+    v.lean = m->tc_launch_cfg.lean;
     cudaError_t e = cudaSuccess;
     with_kernel(v, [&](auto fn) { e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });
     if (e != cudaSuccess) { *why = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e); return TABNET_ERR_CUDA; }
@@ -1158,7 +1221,7 @@ cudaError_t tc_launch(tabnet_model* m, const float* x_num, const int* x_cat, int
     // a segmented launch learns its row count on the device: one CTA per slot
     const unsigned grid = (unsigned)(seg ? slots : std::min<int64_t>((rows + 127) / 128, slots));
     const dim3 block(128 * L.nwg);
-    const Variant v{p.m.N, L.nwg, m->precision == TABNET_BF16X3, L.zreg};
+    const Variant v{p.m.N, L.nwg, m->precision == TABNET_BF16X3, L.zreg, L.lean};
     const bool found = with_kernel(v, [&](auto fn) {
         fn<<<grid, block, L.smem, stream>>>(p, x_num, x_cat, rows, logits, masks, agg);
     });
