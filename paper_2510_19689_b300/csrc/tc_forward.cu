@@ -58,7 +58,8 @@ constexpr float kSqrtHalf = 0.70710678118654752440f;
 constexpr int kMaxClasses = 4;
 constexpr int kFStride = 129;  // row stride (floats) of the input cache: transposed writes hit distinct banks
 // sparsemax input kept in registers: up to this many 16-column chunks per thread
-__host__ __device__ constexpr int zreg_chunks(int nwg) { return nwg == 1 ? 3 : 2; }
+// (two warpgroups per row keep z in TMEM: their register budget is 128)
+__host__ __device__ constexpr int zreg_chunks(int nwg) { return nwg == 1 ? 3 : 0; }
 
 #ifdef TABNET_TRACE
 #define TC_TRACE(i, v)                                                          \
@@ -155,6 +156,25 @@ __device__ __forceinline__ void store_a16(uint8_t* sA, uint8_t* sAlo, int r, int
     }
 }
 
+// Row r, K columns [8 u, 8 u + 8) of the A operand (u = 8-column unit).
+template <bool SPLIT>
+__device__ __forceinline__ void store_a8(uint8_t* sA, uint8_t* sAlo, int r, int u, const float (&v)[8]) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
+    const uint32_t o = (uint32_t)((u >> 3) * 16384) + sw128_off(r, u & 7);
+    *reinterpret_cast<uint4*>(sA + o) = make_uint4(w[0], w[1], w[2], w[3]);
+    if constexpr (SPLIT) {
+        uint32_t l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 hf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[j]));
+            l[j] = pack_bf16(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+        }
+        *reinterpret_cast<uint4*>(sAlo + o) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
 // Folded-BN vectors: staged in shared memory (epi_s != 0, a shared address)
 // or read through the read-only path from global memory.
 template <bool STAGED>
@@ -163,9 +183,9 @@ __device__ __forceinline__ float4 ld_epi(const float* g, uint32_t epi_s, int idx
     return __ldg(reinterpret_cast<const float4*>(g + idx));
 }
 
-// LEAN: the launch shape stages the BN shifts, the input cache and the mask
-// stage in shared memory and keeps the aggregate in TMEM, so the kernel is
-// compiled with only those paths (smaller code, fewer instruction misses).
+// LEAN: the launch shape stages the BN shifts and the input cache in shared
+// memory and keeps the aggregate in TMEM, so the kernel is compiled with only
+// those paths (smaller code, fewer instruction misses).
 template <int N, int NWG, bool SPLIT, bool ZREG, bool LEAN>
 __global__ void __launch_bounds__(128 * NWG, (NWG == 2 && N <= 64) ? 2 : 1)
 tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* __restrict__ x_cat,
@@ -504,14 +524,30 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         ptx::tmem_wait_st();
         PH_MARK(0);
         float lacc[kMaxClasses];
-#pragma unroll
-        for (int k = 0; k < kMaxClasses; ++k) lacc[k] = 0.f;
+#pragma unroll 1
+        for (int k = 0; k < n_cls; ++k) lacc[k] = 0.f;
         float res[RCH][16];
 
-        for (int s = 0; s <= m.n_steps && alive; ++s) {
-            if (s > 0) {
+#pragma unroll
+        for (int cc = 0; cc < RCH; ++cc)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) res[cc][j] = 0.f;
+
+        // The tile's MMA chains in order: the step-0 feature transformer's
+        // layers, then per decision step its attentive layer and its feature
+        // transformer's layers (one call site keeps the issue code compact).
+        int s = 0, l = 0;
+        bool att = false;
+#pragma unroll 1
+        while (true) {
+            const bool first = !att && l == 0;
+            if (!run_mma(att ? p.kn_blocks : (first ? p.k0_blocks : p.kn_blocks), (att || !first) ? N / 16 : dch,
+                         att ? idesc_att : idesc_ft)) {
+                alive = false;
+                break;
+            }
+            if (att) {
                 // ---- attentive transformer of step s: z = (W_att a) * scale + shift, times P
-                if (!run_mma(p.kn_blocks, N / 16, idesc_att)) { alive = false; break; }
                 const int ash = n_ft_layers * 2 * N + (s - 1) * p.dp;  // float index of the BN shift
                 auto load_z = [&](int ch, float (&z)[16], uint32_t (&pr)[16]) {
                     uint32_t acc[16];
@@ -532,7 +568,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 };
                 // Sparsemax: Michelot's fixed point tau = (sum_{z > tau} z - 1) / #{z > tau},
                 // from tau = (sum z - 1) / de, until the support stops shrinking.
-                float zr[ZREG ? kZregChunks : 1][16];
+                float zr[(ZREG && kZregChunks > 0) ? kZregChunks : 1][16];
                 float zs = 0.f;
                 if constexpr (ZREG) {
 #pragma unroll
@@ -547,14 +583,20 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                         }
                     }
                 } else {
+                    // z replaces the consumed accumulator columns in TMEM
+#pragma unroll 1
                     for (int ch = wg; ch < dch; ch += NWG) {
                         float z[16];
-                        uint32_t pr[16];
+                        uint32_t pr[16], zu[16];
                         load_z(ch, z, pr);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j)
+                        for (int j = 0; j < 16; ++j) {
                             if (ch * 16 + j < de) zs += z[j];
+                            zu[j] = __float_as_uint(z[j]);
+                        }
+                        ptx::tmem_st16(t_acc + ch * 16, zu);
                     }
+                    ptx::tmem_wait_st();
                 }
                 float tau = (xsum(zs, 0.f).x - 1.f) / (float)de;
                 int prev = de;
@@ -576,13 +618,16 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                             }
                         }
                     } else {
+#pragma unroll 1
                         for (int ch = wg; ch < dch; ch += NWG) {
-                            float z[16];
-                            uint32_t pr[16];
-                            load_z(ch, z, pr);
+                            uint32_t zu[16];
+                            ptx::tmem_ld16(t_acc + ch * 16, zu);
+                            ptx::tmem_wait_ld(zu);
 #pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                if (z[j] > tau) { ss += z[j]; cnt += 1.f; }
+                            for (int j = 0; j < 16; ++j) {
+                                const float z = __uint_as_float(zu[j]);
+                                if (z > tau) { ss += z; cnt += 1.f; }
+                            }
                         }
                     }
                     const float2 t = xsum(ss, cnt);
@@ -605,7 +650,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 PH_MARK(2);
                 // Mask, prior, masked input (A for the step's first FC), outputs.
                 float* mrow = (io.masks && valid) ? io.masks + (size_t)(s - 1) * de : nullptr;
-                float* mst = (LEAN || p.sm.mstage >= 0) ? reinterpret_cast<float*>(smem + p.sm.mstage) : nullptr;
+                float* mst = p.sm.mstage >= 0 ? reinterpret_cast<float*>(smem + p.sm.mstage) : nullptr;
 #pragma unroll 1
                 for (int il = 0; wg + il * NWG < dch; ++il) {
                     const int ch = wg + il * NWG;
@@ -623,7 +668,12 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                             z[j] = zz;
                         }
                     } else {
-                        load_z(ch, z, pr);
+                        uint32_t zu[16];
+                        ptx::tmem_ld16(t_acc + ch * 16, zu);
+                        ptx::tmem_ld16(t_p + ch * 16, pr);
+                        ptx::tmem_wait_ld(zu, pr);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) z[j] = __uint_as_float(zu[j]);
                     }
                     float mk[16], v[16];
                     uint32_t pn[16], mh[8];
@@ -686,62 +736,69 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     }
                 }
                 PH_MARK(3);
+                att = false;
+                continue;
             }
 
-            // ---- feature transformer s
-#pragma unroll 1
-            for (int l = 0; l < lpf; ++l) {
-                const bool first = (l == 0);
-                if (!run_mma(first ? p.k0_blocks : p.kn_blocks, first ? dch : N / 16, idesc_ft)) {
-                    alive = false;
-                    break;
+            // ---- layer l of feature transformer s
+            const int sh = (s * lpf + l) * 2 * N;  // float index of the layer's BN shift
+            // x = sqrt(1/2) (x_prev + g): the linear half of every layer but an
+            // FT's first is packed pre-scaled by sqrt(1/2), so x = x_prev sqrt(1/2) + g
+            const float cres = first ? 0.f : kSqrtHalf;
+            TC_TRACE(128 + tid / 32, 3000 + lc);
+            // One warpgroup alone on a row (NWG = 1) takes 16-column pieces and
+            // requests piece k+1 from TMEM before computing piece k; with two
+            // warpgroups per row, 8-column pieces loaded one at a time keep
+            // the register count within the two-CTAs-per-SM budget.
+            constexpr int SW = NWG == 1 ? 16 : 8;
+            constexpr int NSUB = CPW / SW;
+            uint32_t lin[NWG == 1 ? 2 : 1][SW], gat[NWG == 1 ? 2 : 1][SW];
+            ptx::tmem_ld_cols<SW>(t_acc + wg * CPW, lin[0]);
+            ptx::tmem_ld_cols<SW>(t_acc + N + wg * CPW, gat[0]);
+            ptx::tmem_wait_ld(lin[0], gat[0]);
+            PH_MARK(14);
+#pragma unroll
+            for (int sc = 0; sc < NSUB; ++sc) {
+                const int c0 = wg * CPW + sc * SW;
+                const int cur = NWG == 1 ? (sc & 1) : 0;
+                if constexpr (NWG == 1) {
+                    if (sc + 1 < NSUB) {
+                        ptx::tmem_ld_cols<SW>(t_acc + c0 + SW, lin[cur ^ 1]);
+                        ptx::tmem_ld_cols<SW>(t_acc + N + c0 + SW, gat[cur ^ 1]);
+                    }
+                } else if (sc > 0) {
+                    ptx::tmem_ld_cols<SW>(t_acc + c0, lin[0]);
+                    ptx::tmem_ld_cols<SW>(t_acc + N + c0, gat[0]);
+                    ptx::tmem_wait_ld(lin[0], gat[0]);
                 }
-                const int sh = (s * lpf + l) * 2 * N;  // float index of the layer's BN shift
-                TC_TRACE(128 + tid / 32, 3000 + lc);
-                // TMEM loads run one chunk ahead of the arithmetic: chunk cc+1
-                // is requested before chunk cc is computed, and waited for after.
-                uint32_t lin[2][16], gat[2][16];
-                ptx::tmem_ld16(t_acc + wg * CPW, lin[0]);
-                ptx::tmem_ld16(t_acc + N + wg * CPW, gat[0]);
-                ptx::tmem_wait_ld(lin[0], gat[0]);
-                PH_MARK(14);
+                float out[SW];
 #pragma unroll
-                for (int cc = 0; cc < RCH; ++cc) {
-                    const int c0 = wg * CPW + cc * 16;
-                    const int cur = cc & 1;
-                    if (cc + 1 < RCH) {
-                        ptx::tmem_ld16(t_acc + c0 + 16, lin[cur ^ 1]);
-                        ptx::tmem_ld16(t_acc + N + c0 + 16, gat[cur ^ 1]);
+                for (int q = 0; q < SW / 4; ++q) {
+                    const float4 hl = ld_epi<LEAN>(epi, epi_s, sh + c0 + 4 * q);
+                    const float4 hg = ld_epi<LEAN>(epi, epi_s, sh + N + c0 + 4 * q);
+                    const float hlv[4] = {hl.x, hl.y, hl.z, hl.w};
+                    const float hgv[4] = {hg.x, hg.y, hg.z, hg.w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int j = 4 * q + t;
+                        float& r = res[(sc * SW + j) / 16][(sc * SW + j) % 16];
+                        const float ul = __uint_as_float(lin[cur][j]) + hlv[t];
+                        const float ug = __uint_as_float(gat[cur][j]) + hgv[t];
+                        const float g = ul * (SPLIT ? sigmoid_from_log2(ug) : sigmoid_fast(ug));
+                        const float x = fmaf(r, cres, g);
+                        r = x;
+                        out[j] = x;
                     }
-                    float4 hl4[4], hg4[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        hl4[q] = ld_epi<LEAN>(epi, epi_s, sh + c0 + 4 * q);
-                        hg4[q] = ld_epi<LEAN>(epi, epi_s, sh + N + c0 + 4 * q);
-                    }
-                    float out[16];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float hlv[4] = {hl4[q].x, hl4[q].y, hl4[q].z, hl4[q].w};
-                        const float hgv[4] = {hg4[q].x, hg4[q].y, hg4[q].z, hg4[q].w};
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            const int j = 4 * q + t;
-                            const float ul = __uint_as_float(lin[cur][j]) + hlv[t];
-                            const float ug = __uint_as_float(gat[cur][j]) + hgv[t];
-                            const float g = ul * (SPLIT ? sigmoid_from_log2(ug) : sigmoid_fast(ug));
-                            const float x = first ? g : (res[cc][j] + g) * kSqrtHalf;
-                            res[cc][j] = x;
-                            out[j] = x;
-                        }
-                    }
-                    if (cc + 1 < RCH) ptx::tmem_wait_ld(lin[cur ^ 1], gat[cur ^ 1]);
-                    store_a16<SPLIT>(sA, sAlo, lt, c0 / 16, out);
                 }
-                PH_MARK(4);
+                if constexpr (NWG == 1) {
+                    if (sc + 1 < NSUB) ptx::tmem_wait_ld(lin[cur ^ 1], gat[cur ^ 1]);
+                }
+                if constexpr (SW == 16) store_a16<SPLIT>(sA, sAlo, lt, c0 / 16, out);
+                else store_a8<SPLIT>(sA, sAlo, lt, c0 / 8, out);
             }
-            if (!alive) break;
-
+            PH_MARK(4);
+            if (++l < lpf) continue;
+            l = 0;
             if (s > 0) {
                 // ---- decision output: acc += ReLU(d) (folded into the logits), eta, aggregate
                 // res becomes ReLU(d) (zero on the attention columns): the next
@@ -757,24 +814,23 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                         eta += dv;
                     }
                 }
-                // logits += W_f ReLU(d), W_f staged as [class][N] with zero columns past n_d
+                // logits += W_f ReLU(d), W_f staged as [class][N] with zero columns
+                // past n_d; one class per pass (the per-class sums live in local memory)
+#pragma unroll 1
+                for (int k = 0; k < n_cls; ++k) {
+                    float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-                for (int k = 0; k < kMaxClasses; ++k) {
-                    if (k < n_cls) {
-                        float a0 = 0.f, a1 = 0.f;
+                    for (int cc = 0; cc < RCH; ++cc) {
 #pragma unroll
-                        for (int cc = 0; cc < RCH; ++cc) {
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const float4 w = ptx::ld_shared_f4(wf_s + 4u * (uint32_t)(k * N + wg * CPW + cc * 16 + 4 * q));
-                                a0 = fmaf(w.x, res[cc][4 * q], a0);
-                                a1 = fmaf(w.y, res[cc][4 * q + 1], a1);
-                                a0 = fmaf(w.z, res[cc][4 * q + 2], a0);
-                                a1 = fmaf(w.w, res[cc][4 * q + 3], a1);
-                            }
+                        for (int q = 0; q < 4; ++q) {
+                            const float4 w = ptx::ld_shared_f4(wf_s + 4u * (uint32_t)(k * N + wg * CPW + cc * 16 + 4 * q));
+                            a0 = fmaf(w.x, res[cc][4 * q], a0);
+                            a1 = fmaf(w.y, res[cc][4 * q + 1], a1);
+                            a0 = fmaf(w.z, res[cc][4 * q + 2], a0);
+                            a1 = fmaf(w.w, res[cc][4 * q + 3], a1);
                         }
-                        lacc[k] += a0 + a1;
                     }
+                    lacc[k] += a0 + a1;
                 }
                 eta = xsum(eta, 0.f).x;
                 PH_MARK(5);
@@ -819,16 +875,16 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 }
                 PH_MARK(5);
             }
+            if (++s > m.n_steps) break;
+            att = true;
         }
         if (!alive) break;
 
         // ---- logits and the normalised aggregate
-#pragma unroll
-        for (int k = 0; k < kMaxClasses; ++k) {
-            if (k < n_cls) {
-                const float v = xsum(lacc[k], 0.f).x;
-                if (wg == 0 && valid) io.logits[k] = v + __ldg(m.bf + k);
-            }
+#pragma unroll 1
+        for (int k = 0; k < n_cls; ++k) {
+            const float v = xsum(lacc[k], 0.f).x;
+            if (wg == 0 && valid) io.logits[k] = v + __ldg(m.bf + k);
         }
         if (agg_tmem) {
             // one column per feature: normalise the TMEM aggregate directly
@@ -953,13 +1009,19 @@ bool with_kernel(const Variant& v, F&& f) {
         TC_VAR4(NN, WW, false, true)    \
         TC_VAR4(NN, WW, false, false)   \
     }
+#define TC_VARIANT_NOZ(NN, WW)          \
+    if (v.N == NN && v.nwg == WW) {     \
+        TC_VAR4(NN, WW, true, false)    \
+        TC_VAR4(NN, WW, false, false)   \
+    }
     TC_VARIANT(16, 1)
     TC_VARIANT(32, 1)
-    TC_VARIANT(32, 2)
+    TC_VARIANT_NOZ(32, 2)
     TC_VARIANT(64, 1)
-    TC_VARIANT(64, 2)
-    TC_VARIANT(128, 2)
+    TC_VARIANT_NOZ(64, 2)
+    TC_VARIANT_NOZ(128, 2)
 #undef TC_VARIANT
+#undef TC_VARIANT_NOZ
 #undef TC_VAR4
     return false;
 }
@@ -1077,6 +1139,14 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
             GluLayer g = hm.layer(s, l);
             std::vector<float> sc, sh;
             fold_bn(*g.bn, d.bn_eps, sc, sh);
+            if (l > 0) {
+                // linear half pre-scaled by sqrt(1/2): the kernel forms the
+                // residual sqrt(1/2) (x + g) as x sqrt(1/2) + g
+                for (int n = 0; n < N; ++n) {
+                    sc[n] = (float)((double)sc[n] * 0.70710678118654752440);
+                    sh[n] = (float)((double)sh[n] * 0.70710678118654752440);
+                }
+            }
             if (split) {
                 // gate half pre-scaled by -log2(e): the kernel's sigmoid takes 2^(-x log2 e) directly
                 for (int n = N; n < 2 * N; ++n) {
@@ -1186,7 +1256,7 @@ int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std
     m->tc_launch_cfg.ctas_per_sm = best_cps;
     m->tc_launch_cfg.smem = smem;
     m->tc_launch_cfg.zreg = zreg;
-    m->tc_launch_cfg.lean = p.tm_agg >= 0 && best_epi && best_f && best_mst;
+    m->tc_launch_cfg.lean = p.tm_agg >= 0 && best_epi && best_f;
     v.lean = m->tc_launch_cfg.lean;
     cudaError_t e = cudaSuccess;
     with_kernel(v, [&](auto fn) { e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });

@@ -216,6 +216,19 @@ __device__ __forceinline__ void tmem_wait_ld8(uint32_t (&r)[8]) {
                    "+r"(r[7])::"memory");
 }
 
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&a)[8], uint32_t (&b)[8]) {
+    tmem_wait_ld8(a);
+    asm volatile("" : "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]));
+}
+
+// W (8 or 16) consecutive 32-bit TMEM columns of this thread's lane.
+template <int W>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[W]) {
+    static_assert(W == 8 || W == 16, "8 or 16 columns");
+    if constexpr (W == 16) tmem_ld16(taddr, r);
+    else tmem_ld8(taddr, r);
+}
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
     __syncwarp();  // .sync.aligned: the whole warp, converged
     asm volatile(

@@ -38,7 +38,9 @@ def _req(name, rows, seed):
 
 def test_same_result_alone_and_in_a_mix(models):
     tabnet, params, ms = models
-    srv = tabnet.Server(ms, device_bytes=256 << 20)
+    # one batch in flight at a time: requests that arrive meanwhile queue up
+    # and leave together in the next batch
+    srv = tabnet.Server(ms, device_bytes=256 << 20, max_inflight_batches=1)
     targets = [(i, *_req(n, r, 100 + i)) for i, (n, r) in enumerate(zip(NAMES, [37, 300, 129]))]
     alone = []
     for i, xn, xc in targets:
@@ -48,10 +50,12 @@ def test_same_result_alone_and_in_a_mix(models):
         srv.release(t)
     # the same requests again, each in the middle of a burst of other requests
     rng = np.random.default_rng(5)
-    tickets, mine = [], {}
+    burst = []
     for k in range(300):
         i = int(rng.integers(3))
-        xn, xc = _req(NAMES[i], int(rng.integers(1, 200)), 1000 + k)
+        burst.append((i, *_req(NAMES[i], int(rng.integers(1, 200)), 1000 + k)))
+    tickets, mine = [], {}
+    for k, (i, xn, xc) in enumerate(burst):
         tickets.append(srv.submit(i, xn, xc))
         if k in (100, 150, 200):
             j = (100, 150, 200).index(k)
