@@ -269,28 +269,36 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     // of a tile's sequence.
     int64_t g_issue = 0, g_cons = 0;  // chunks issued / consumed so far
     int is_slot = 0, is_chunk = 0;    // slot and per-tile index of chunk g_issue
-    uint32_t is_round = 0;            // round of chunk g_issue
     int cs_slot = 0;                  // slot of chunk g_cons
     uint32_t cs_round = 0;            // round of chunk g_cons
+    // Slots whose release is signalled on their own "empty" barrier (a K
+    // block followed by more blocks of the same layer) and the parity to wait
+    // for; the last block's slots are released by the accumulator barrier.
+    uint32_t empty_pending = 0, empty_par = 0;
     bool acc_outstanding = false;
     uint32_t acc_phase = 0;
     int xc = 0;
     int lc = 0;  // layers run by this CTA
 
-    // Thread 0: start the copy of chunk g_issue once its slot is free (its
-    // previous occupant, round is_round - 1, has been read by the MMAs).
+    // Thread 0: start the copy of chunk g_issue once its slot is free (the
+    // MMAs that read its previous occupant have completed).
     auto issue_next = [&]() -> bool {
         const int slot = is_slot;
-        if (is_round > 0 && !ptx::mbar_wait(bar_empty + 8 * slot, (is_round - 1) & 1u, kWaitLimit)) {
-            note_timeout(m.status, 5, (unsigned)g_issue);
-            return false;
+        if (empty_pending & (1u << slot)) {
+            if (!ptx::mbar_wait(bar_empty + 8 * slot, (empty_par >> slot) & 1u, kWaitLimit)) {
+                note_timeout(m.status, 5, (unsigned)g_issue);
+                return false;
+            }
+            empty_par ^= 1u << slot;
+            empty_pending &= ~(1u << slot);
         }
+        PH_MARK(8);
         const uint2 ck = sChunks[is_chunk];
         ptx::mbar_arrive_expect_tx(bar_full + 8 * slot, ck.y);
         ptx::bulk_g2s(ring_base + (uint32_t)(slot * p.slot_bytes), p.wbase + ck.x, ck.y, bar_full + 8 * slot);
         ++g_issue;
         if (++is_chunk == p.chunks_per_tile) is_chunk = 0;
-        if (++is_slot == S) { is_slot = 0; ++is_round; }
+        if (++is_slot == S) is_slot = 0;
         return true;
     };
     if (tid == 0)
@@ -354,7 +362,12 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 }
                 kk += nk;
 #pragma unroll
-                for (int part = 0; part < PARTS; ++part) ptx::mma_commit(bar_empty + 8 * slot_p[part]);
+                for (int part = 0; part < PARTS; ++part) {
+                    if (b + 1 < kblocks) {
+                        ptx::mma_commit(bar_empty + 8 * slot_p[part]);
+                        empty_pending |= 1u << slot_p[part];
+                    }
+                }
                 g_cons += PARTS;
 #pragma unroll
                 for (int part = 0; part < PARTS; ++part)
@@ -414,6 +427,22 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     for (int64_t tile = blockIdx.x; tile < num_tiles && alive; tile += gridDim.x) {
         const RowIO io = row_io(p.seg, m, tile * 128 + lt, total, x_num, x_cat, logits, masks, agg_out);
         const bool valid = io.valid;
+        // warm L2 with this thread's row of the CTA's next tile: that tile's
+        // input gather then waits on L2 rather than DRAM
+        if (tile + gridDim.x < num_tiles) {
+            const RowIO nx = row_io(p.seg, m, (tile + gridDim.x) * 128 + lt, total, x_num, x_cat, logits, nullptr,
+                                    nullptr);
+            if (nx.valid) {
+                if (nx.x_num && m.n_num > 0) {
+                    ptx::prefetch_l2(nx.x_num);
+                    ptx::prefetch_l2(nx.x_num + m.n_num - 1);
+                }
+                if (nx.x_cat && m.n_cat > 0) {
+                    ptx::prefetch_l2(nx.x_cat);
+                    ptx::prefetch_l2(nx.x_cat + m.n_cat - 1);
+                }
+            }
+        }
 
         // Embedded, BN'd input value of column c for this row.
         auto f_value = [&](int c, bool check) -> float {
@@ -852,7 +881,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                         ptx::tmem_st16(t_agg + ch * 16, ag);
                     }
                     ptx::tmem_wait_st();
-                    PH_MARK(15);
+                    PH_MARK(5);
                 } else
                 for (int ch = wg; ch < dch; ch += NWG) {
                     uint32_t mh[8];
@@ -937,6 +966,10 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         }
         if (acc_outstanding && !ptx::mbar_wait(bar_acc, acc_phase ^ 1, kWaitLimit))
             note_timeout(m.status, 4, (unsigned)lc);
+        for (int sl2 = 0; sl2 < S; ++sl2)
+            if ((empty_pending >> sl2) & 1u)
+                if (!ptx::mbar_wait(bar_empty + 8 * sl2, (empty_par >> sl2) & 1u, kWaitLimit))
+                    note_timeout(m.status, 6, (unsigned)sl2);
     }
     ptx::tc_fence_before();
     __syncthreads();
