@@ -304,16 +304,12 @@ def main():
         return
     import numpy as np
     import torch
-    from paper_2510_19689_b300 import autotune, synth, tabnet
+    from paper_2510_19689_b300 import autotune, replicas, synth, tabnet
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    # one process per GPU; rows are independent, so each rank runs its own
+    # replica on its own batch (weak scaling, no collective in the step)
+    group = replicas.Group("nccl")
+    world, rank, local = group.world, group.rank, group.local
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     name = args.workload
@@ -364,8 +360,7 @@ def main():
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    group.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -375,15 +370,10 @@ def main():
             step(k)
         e1.record(stream)
         e1.synchronize()
-    if dist:
-        dist.barrier()
-    ms_total = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    group.barrier()
+    ms_total = group.max(e0.elapsed_time(e1))
     ms_step = ms_total / args.steps
-    value = world * rows * args.steps / (ms_total / 1e3)
+    value = replicas.throughput(group.sum(rows * args.steps), ms_total)
     clocks = clk.summary()
 
     extras = {}
@@ -486,8 +476,7 @@ def main():
         line.update(extras)
         print(json.dumps(line), flush=True)
     model.close()
-    if dist:
-        dist.destroy_process_group()
+    group.close()
 
 
 if __name__ == "__main__":
