@@ -1098,7 +1098,7 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
     const int dp = round_up(d.d_emb, 16);
     const bool split = (m->precision == TABNET_BF16X3);
     if (m->precision != TABNET_BF16 && m->precision != TABNET_BF16X3) {
-        *why = "fp8 tensor-core path not built";
+        *why = "FP8 E4M3 is not offered: E4M3 operands move the sparsemax masks of most rows";
         return TABNET_ERR_UNSUPPORTED_DIMS;
     }
     if (N != 16 && N != 32 && N != 64 && N != 128) {
