@@ -238,7 +238,7 @@ int tabnet_get_tile_config(const tabnet_model* model, int* nwg, int* n_slots, in
 /* ---------------------------------------------------------------- serving
  * A continuous-batching request server over resident models on one GPU (the
  * paper's GPU functions keep the model in GPU memory and serve batches of
- * records per invocation, Sec. III-B, judged by p50/p95/p99 latency,
+ * records per invocation, Sec. III-B, measured by p50/p95/p99 latency,
  * Sec. IV-C).  An engine thread owned by the server packs every request
  * that has arrived for a model into one batch in that model's device ring
  * (admission by device memory: a request waits while the ring is full), runs

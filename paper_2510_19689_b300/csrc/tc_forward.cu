@@ -416,6 +416,20 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         }
     };
 
+    // (sum of a, max of b) over the warpgroups sharing a row
+    auto xsummax = [&](float a, float b) -> float2 {
+        if constexpr (NWG == 1) {
+            return make_float2(a, b);
+        } else {
+            float2* slot = sX + (xc & 1) * 256;
+            slot[wg * 128 + lt] = make_float2(a, b);
+            ptx::named_bar_sync(1, THREADS);
+            const float2 o = slot[(wg ^ 1) * 128 + lt];
+            ++xc;
+            return make_float2(wg == 0 ? a + o.x : o.x + a, fmaxf(b, o.y));
+        }
+    };
+
     const int de = m.de, dch = p.dp / 16, n_d = m.n_d, n_cls = m.n_classes;
     const float gamma = m.gamma;
     const uint32_t idesc_ft = ptx::idesc_bf16(2 * N);
@@ -595,10 +609,14 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                         }
                     }
                 };
-                // Sparsemax: Michelot's fixed point tau = (sum_{z > tau} z - 1) / #{z > tau},
-                // from tau = (sum z - 1) / de, until the support stops shrinking.
+                // Sparsemax: Michelot's fixed point tau = (sum_{z > tau} z - 1) / #{z > tau}
+                // until the support stops changing, started from the larger of two
+                // lower bounds of the threshold, (sum z - 1) / de and max z - 1 (the
+                // mask's mass 1 is at least max z - tau): sparse masks, i.e. most,
+                // then converge in a pass or two.  From any start the iterates reach
+                // the same support, so the threshold and mask do not depend on it.
                 float zr[(ZREG && kZregChunks > 0) ? kZregChunks : 1][16];
-                float zs = 0.f;
+                float zs = 0.f, zmax = -INFINITY;
                 if constexpr (ZREG) {
 #pragma unroll
                     for (int il = 0; il < kZregChunks; ++il) {
@@ -607,8 +625,10 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                             uint32_t pr[16];
                             load_z(ch, zr[il], pr);
 #pragma unroll
-                            for (int j = 0; j < 16; ++j)
+                            for (int j = 0; j < 16; ++j) {
                                 if (ch * 16 + j < de) zs += zr[il][j];
+                                zmax = fmaxf(zmax, zr[il][j]);
+                            }
                         }
                     }
                 } else {
@@ -621,13 +641,15 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             if (ch * 16 + j < de) zs += z[j];
+                            zmax = fmaxf(zmax, z[j]);
                             zu[j] = __float_as_uint(z[j]);
                         }
                         ptx::tmem_st16(t_acc + ch * 16, zu);
                     }
                     ptx::tmem_wait_st();
                 }
-                float tau = (xsum(zs, 0.f).x - 1.f) / (float)de;
+                const float2 zsm = xsummax(zs, zmax);
+                float tau = fmaxf((zsm.x - 1.f) / (float)de, zsm.y - 1.f);
                 int prev = de;
                 bool done = false;
                 // Rows converge after different numbers of passes, but TMEM
