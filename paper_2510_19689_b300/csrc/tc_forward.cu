@@ -528,14 +528,25 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                             const int* cr = sRowC[i0 + i];
                             iv[i] = cr ? __ldg(cr + j) : 0;
                         }
-#pragma unroll 1
+                        unsigned oob = 0;  // bit i: row i0 + i has an out-of-range index
+#pragma unroll
                         for (int i = 0; i < G; ++i) {
-                            const bool oob = iv[i] < 0 || iv[i] >= card;
-                            if (oob && sRowC[i0 + i]) atomicOr(m.status, TABNET_STATUS_CAT_OOB);
+                            if (iv[i] < 0 || iv[i] >= card) {
+                                oob |= 1u << i;
+                                if (sRowC[i0 + i]) atomicOr(m.status, TABNET_STATUS_CAT_OOB);
+                            }
+                        }
+                        // the rows' embedding values are loaded together, one
+                        // embedding column at a time
 #pragma unroll 1
-                            for (int e = 0; e < len; ++e)
-                                fc[(c0 + e) * kFStride + i0 + i] =
-                                    oob ? __ldg(m.t0 + c0 + e) : __ldg(tab + (size_t)iv[i] * len + e);
+                        for (int e = 0; e < len; ++e) {
+                            const float t0e = __ldg(m.t0 + c0 + e);
+                            float v[G];
+#pragma unroll
+                            for (int i = 0; i < G; ++i)
+                                v[i] = ((oob >> i) & 1u) ? t0e : __ldg(tab + (size_t)iv[i] * len + e);
+#pragma unroll
+                            for (int i = 0; i < G; ++i) fc[(c0 + e) * kFStride + i0 + i] = v[i];
                         }
                     }
                 }
