@@ -494,23 +494,20 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             }
             __syncthreads();
             const int lane = tid & 31, r0 = warp * RPW;
-            constexpr int G = 8;  // rows whose loads are in flight together
 #pragma unroll 1
             for (int cb = 0; cb < m.n_num; cb += 32) {
                 const int c = cb + lane;
                 if (c < m.n_num) {
                     const float s0 = __ldg(m.s0 + c), t0 = __ldg(m.t0 + c);
-#pragma unroll 1
-                    for (int i0 = r0; i0 < r0 + RPW; i0 += G) {
-                        float xv[G];
+                    // every row of the warp's share in flight at once
+                    float xv[RPW];
 #pragma unroll
-                        for (int i = 0; i < G; ++i) {
-                            const float* xr = sRowX[i0 + i];
-                            xv[i] = xr ? __ldg(xr + c) : 0.f;
-                        }
-#pragma unroll
-                        for (int i = 0; i < G; ++i) fc[c * kFStride + i0 + i] = fmaf(s0, xv[i], t0);
+                    for (int i = 0; i < RPW; ++i) {
+                        const float* xr = sRowX[r0 + i];
+                        xv[i] = xr ? __ldg(xr + c) : 0.f;
                     }
+#pragma unroll
+                    for (int i = 0; i < RPW; ++i) fc[c * kFStride + r0 + i] = fmaf(s0, xv[i], t0);
                 }
             }
 #pragma unroll 1
@@ -520,6 +517,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     const int card = __ldg(m.cat_card + j);
                     const int c0 = __ldg(m.feat_col + m.n_num + j), len = __ldg(m.feat_len + m.n_num + j);
                     const float* tab = m.emb + __ldg(m.cat_off + j);
+                    constexpr int G = RPW;  // every row of the warp's share in flight at once
 #pragma unroll 1
                     for (int i0 = r0; i0 < r0 + RPW; i0 += G) {
                         int iv[G];
