@@ -710,7 +710,12 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 PH_MARK(2);
                 // Mask, prior, masked input (A for the step's first FC), outputs.
                 float* mrow = (io.masks && valid) ? io.masks + (size_t)(s - 1) * de : nullptr;
-                float* mst = p.sm.mstage >= 0 ? reinterpret_cast<float*>(smem + p.sm.mstage) : nullptr;
+                // per-warp staging of a 32-row x 16-column block of masks (row
+                // stride 17: conflict-free both ways), written out as 64-byte
+                // row pieces instead of one 4-byte store per row and column
+                float* mst = p.sm.mstage >= 0 ? reinterpret_cast<float*>(smem + p.sm.mstage) + warp * (32 * 17)
+                                              : nullptr;
+                float* const* sRowM = reinterpret_cast<float* const*>(smem + p.sm.rowp + 128 * 16);
 #pragma unroll 1
                 for (int il = 0; wg + il * NWG < dch; ++il) {
                     const int ch = wg + il * NWG;
@@ -759,10 +764,19 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                         }
                     }
                     if (mst) {
-                        // staged: written out row by row below
+                        const int lane = tid & 31;
 #pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (ch * 16 + j < de) mst[(ch * 16 + j) * kFStride + lt] = mk[j];
+                        for (int j = 0; j < 16; ++j) mst[lane * 17 + j] = mk[j];
+                        __syncwarp();
+                        const int ncol = min(16, de - ch * 16), c = lane & 15;
+                        const size_t off = (size_t)(s - 1) * de + ch * 16 + c;
+#pragma unroll 4
+                        for (int i = 0; i < 16; ++i) {
+                            const int r = 2 * i + (lane >> 4);  // row within the warp's 32
+                            float* dst = sRowM[(warp & 3) * 32 + r];
+                            if (dst && c < ncol) dst[off] = mst[r * 17 + c];
+                        }
+                        __syncwarp();
                     } else if (mrow) {
                         if (((de & 3) == 0) && ((reinterpret_cast<uintptr_t>(mrow) & 15) == 0) && ch * 16 + 16 <= de) {
                             float4* d4 = reinterpret_cast<float4*>(mrow + ch * 16);
@@ -778,23 +792,6 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     store_a16<SPLIT>(sA, sAlo, lt, ch, v);
                 }
                 ptx::tmem_wait_st();
-                if (mst) {
-                    // every warp writes whole rows: lanes walk a row's columns
-                    __syncthreads();
-                    constexpr int RPW = 128 / (4 * NWG);
-                    float** sRowM = reinterpret_cast<float**>(smem + p.sm.rowp + 128 * 16);
-                    const int lane = tid & 31;
-#pragma unroll 1
-                    for (int i = 0; i < RPW; ++i) {
-                        const int r = warp * RPW + i;
-                        float* dst = sRowM[r];
-                        if (dst) {
-                            dst += (size_t)(s - 1) * de;
-#pragma unroll 1
-                            for (int c = lane; c < de; c += 32) dst[c] = mst[c * kFStride + r];
-                        }
-                    }
-                }
                 PH_MARK(3);
                 att = false;
                 continue;
@@ -1112,7 +1109,7 @@ TcSmem smem_layout(int N, int dp, int de, int d, int n_cls, int n_d, int n_slots
     if (with_f) {
         s.fcache = o; o += round_up(de * kFStride * 4, 16);
         s.rowp = o; o += 128 * 24;
-        if (with_mst) { s.mstage = o; o += round_up(de * kFStride * 4, 16); }
+        if (with_mst) { s.mstage = o; o += 4 * nwg * 32 * 17 * 4; }
     }
     s.colf = o; o += round_up(dp * 4, 16);
     s.chunks = o; o += round_up(n_chunks * 8, 16);

@@ -19,7 +19,7 @@ struct TcSmem {
     int epi;    // every layer's folded BN scale/shift (-1: read from global)
     int fcache; // embedded, BN'd input of the tile, float [de][129] (-1: recomputed)
     int rowp;   // with fcache: the tile's row pointers, [128] x_num, [128] x_cat, [128] masks
-    int mstage; // one step's masks of the tile, float [de][129], written out row by row (-1: direct stores)
+    int mstage; // per-warp mask staging, float [warps][32][17] (-1: direct stores)
     int chunks; // the weight-chunk table, uint2 [chunks_per_tile]
     int colf;   // original feature of each embedded column, int [dp]
     int bar;    // mbarriers: n_slots full, n_slots empty, 1 accumulator; TMEM address; abort flag
