@@ -416,6 +416,26 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         }
     };
 
+    // Row-wise outputs leave through the warp's 32 x 16 staging block: this
+    // thread's values v of its row go to columns [base, base + ncol) of
+    // rowptr[row] (a null pointer skips the row), written as 64-byte row
+    // pieces -- two rows per warp store instead of 32 scattered words.
+    float* const mstw = p.sm.mstage >= 0 ? reinterpret_cast<float*>(smem + p.sm.mstage) + warp * (32 * 17) : nullptr;
+    auto stage_store = [&](float* const* rowptr, size_t base, int ncol, const float (&v)[16]) {
+        const int lane = tid & 31;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) mstw[lane * 17 + j] = v[j];
+        __syncwarp();
+        const int c = lane & 15;
+#pragma unroll 4
+        for (int i = 0; i < 16; ++i) {
+            const int r = 2 * i + (lane >> 4);
+            float* dst = rowptr[(warp & 3) * 32 + r];
+            if (dst && c < ncol) dst[base + c] = mstw[r * 17 + c];
+        }
+        __syncwarp();
+    };
+
     // (sum of a, max of b) over the warpgroups sharing a row
     auto xsummax = [&](float a, float b) -> float2 {
         if constexpr (NWG == 1) {
@@ -487,10 +507,12 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             const float** sRowX = reinterpret_cast<const float**>(smem + p.sm.rowp);
             const int** sRowC = reinterpret_cast<const int**>(smem + p.sm.rowp + 128 * 8);
             float** sRowM = reinterpret_cast<float**>(smem + p.sm.rowp + 128 * 16);
+            float** sRowA = reinterpret_cast<float**>(smem + p.sm.rowp + 128 * 24);
             if (wg == 0) {
                 sRowX[lt] = valid ? io.x_num : nullptr;
                 sRowC[lt] = valid ? io.x_cat : nullptr;
                 sRowM[lt] = valid ? io.masks : nullptr;
+                sRowA[lt] = valid ? io.agg : nullptr;
             }
             __syncthreads();
             const int lane = tid & 31, r0 = warp * RPW;
@@ -710,11 +732,6 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 PH_MARK(2);
                 // Mask, prior, masked input (A for the step's first FC), outputs.
                 float* mrow = (io.masks && valid) ? io.masks + (size_t)(s - 1) * de : nullptr;
-                // per-warp staging of a 32-row x 16-column block of masks (row
-                // stride 17: conflict-free both ways), written out as 64-byte
-                // row pieces instead of one 4-byte store per row and column
-                float* mst = p.sm.mstage >= 0 ? reinterpret_cast<float*>(smem + p.sm.mstage) + warp * (32 * 17)
-                                              : nullptr;
                 float* const* sRowM = reinterpret_cast<float* const*>(smem + p.sm.rowp + 128 * 16);
 #pragma unroll 1
                 for (int il = 0; wg + il * NWG < dch; ++il) {
@@ -763,20 +780,8 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                             v[j] = (c < de && mk[j] > 0.f) ? mk[j] * f_value(c, false) : 0.f;
                         }
                     }
-                    if (mst) {
-                        const int lane = tid & 31;
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) mst[lane * 17 + j] = mk[j];
-                        __syncwarp();
-                        const int ncol = min(16, de - ch * 16), c = lane & 15;
-                        const size_t off = (size_t)(s - 1) * de + ch * 16 + c;
-#pragma unroll 4
-                        for (int i = 0; i < 16; ++i) {
-                            const int r = 2 * i + (lane >> 4);  // row within the warp's 32
-                            float* dst = sRowM[(warp & 3) * 32 + r];
-                            if (dst && c < ncol) dst[off] = mst[r * 17 + c];
-                        }
-                        __syncwarp();
+                    if (mstw) {
+                        stage_store(sRowM, (size_t)(s - 1) * de + ch * 16, min(16, de - ch * 16), mk);
                     } else if (mrow) {
                         if (((de & 3) == 0) && ((reinterpret_cast<uintptr_t>(mrow) & 15) == 0) && ch * 16 + 16 <= de) {
                             float4* d4 = reinterpret_cast<float4*>(mrow + ch * 16);
@@ -957,12 +962,18 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             }
             tot = xsum(tot, 0.f).x;
             const float inv = tot > 0.f ? 1.f / tot : 0.f;
+            float* const* sRowA = reinterpret_cast<float* const*>(smem + p.sm.rowp + 128 * 24);
 #pragma unroll 1
             for (int ch = wg; ch < dch; ch += NWG) {
                 uint32_t ag[16];
                 ptx::tmem_ld16(t_agg + ch * 16, ag);
                 ptx::tmem_wait_ld(ag);
-                if (io.agg && valid) {
+                if (mstw) {
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = tot > 0.f ? __uint_as_float(ag[j]) * inv : 0.f;
+                    stage_store(sRowA, ch * 16, min(16, de - ch * 16), v);
+                } else if (io.agg && valid) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
                         if (ch * 16 + j < de) io.agg[ch * 16 + j] = tot > 0.f ? __uint_as_float(ag[j]) * inv : 0.f;
@@ -973,8 +984,17 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             float tot = 0.f;
             for (int j = wg; j < m.d; j += NWG) tot += sAgg[j * 128 + lt];
             tot = xsum(tot, 0.f).x;
-            if (io.agg && valid) {
-                const float inv = tot > 0.f ? 1.f / tot : 0.f;
+            const float inv = tot > 0.f ? 1.f / tot : 0.f;
+            if (mstw) {
+                float* const* sRowA = reinterpret_cast<float* const*>(smem + p.sm.rowp + 128 * 24);
+#pragma unroll 1
+                for (int cb = wg * 16; cb < m.d; cb += 16 * NWG) {
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = (cb + j < m.d && tot > 0.f) ? sAgg[(cb + j) * 128 + lt] * inv : 0.f;
+                    stage_store(sRowA, cb, min(16, m.d - cb), v);
+                }
+            } else if (io.agg && valid) {
                 for (int j = wg; j < m.d; j += NWG) io.agg[j] = tot > 0.f ? sAgg[j * 128 + lt] * inv : 0.f;
             }
         }
@@ -1108,7 +1128,7 @@ TcSmem smem_layout(int N, int dp, int de, int d, int n_cls, int n_d, int n_slots
     s.mstage = -1;
     if (with_f) {
         s.fcache = o; o += round_up(de * kFStride * 4, 16);
-        s.rowp = o; o += 128 * 24;
+        s.rowp = o; o += 128 * 32;
         if (with_mst) { s.mstage = o; o += 4 * nwg * 32 * 17 * 4; }
     }
     s.colf = o; o += round_up(dp * 4, 16);
