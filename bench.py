@@ -260,6 +260,33 @@ def bench_batching(model, params, dev, stream, n_segs=4096, max_rows=4096, reps=
                                          "(prefix-sum scan + forward)"}
 
 
+def fp8_gemm_peak(dev, n=8192, reps=10):
+    """Dense E4M3 x E4M3 -> bf16 GEMM rate of this GPU through PyTorch's scaled
+    matmul (cuBLASLt), n^3, best of `reps`: the FP8 tensor peak a fused FP8
+    path would be measured against (no such path is offered; see the
+    rounding study)."""
+    import torch
+    try:
+        a = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device=dev)
+        for _ in range(3):
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return {"value": 2.0 * n ** 3 / (best / 1e3) / 1e12, "unit": "TFLOP/s",
+                "how": f"torch._scaled_mm e4m3 {n}^3, best of {reps}"}
+    except Exception as exc:  # an older PyTorch without the scaled matmul
+        return {"value": None, "unavailable": str(exc)[:200]}
+
+
 def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), seconds=1.0):
     """Poisson arrivals at each rate for `seconds`, request sizes
     floor(exp(U(0, ln 513))) in [1, 512] rows, the three model shapes
@@ -363,14 +390,21 @@ def main():
     group.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    # an event after every step (recorded on the stream, no synchronisation)
+    # gives the per-step spread; the total is e0 -> e1 as always
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     with ClockSampler(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
         e0.record(stream)
         for k in range(args.steps):
             step(k)
+            marks[k].record(stream)
         e1.record(stream)
         e1.synchronize()
     group.barrier()
+    per_step = [e0.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k]) for k in range(1, args.steps)]
+    step_stats = {"min": float(np.min(per_step)), "median": float(np.median(per_step)),
+                  "max": float(np.max(per_step))}
     ms_total = group.max(e0.elapsed_time(e1))
     ms_step = ms_total / args.steps
     value = replicas.throughput(group.sum(rows * args.steps), ms_total)
@@ -415,6 +449,20 @@ def main():
         r, cores, dt = oracle_rows_per_s(params, x_num_h[:n_cpu], x_cat_h[:n_cpu])
         extras["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                   "sample": f"first {n_cpu} rows of the {name} batch, float64 numpy ({dt:.1f} s)"}
+        # the same oracle held to one host thread (a child process whose BLAS
+        # pools are limited by the environment before numpy loads)
+        n1 = n_cpu // 4
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        code = ("import sys, time, json; sys.path.insert(0, %r); from paper_2510_19689_b300 import synth; "
+                "from oracle import tabnet_oracle as O; p, _, xn, xc = synth.load_config(%r, rows=%d); "
+                "t = time.perf_counter(); O.forward(p, xn, xc); dt = time.perf_counter() - t; "
+                "print(json.dumps([%d / dt, dt]))") % (ROOT, name, n1, n1)
+        try:
+            out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+            r1, dt1 = json.loads(out.stdout.strip().splitlines()[-1])
+            extras["cpu_baseline"]["one_core"] = {"value": r1, "sample": f"first {n1} rows ({dt1:.1f} s)"}
+        except Exception as exc:
+            extras["cpu_baseline"]["one_core"] = {"value": None, "unavailable": str(exc)[:200]}
         # plain FP32 unfused GPU forward (PyTorch eager, TF32 off): the 5x target's divisor
         from paper_2510_19689_b300.unfused import UnfusedTabNet
         un = UnfusedTabNet(params, dev)
@@ -454,6 +502,9 @@ def main():
             extras[f"fused_{prec}"] = {"value": rows / (b0.elapsed_time(b1) / reps / 1e3), "unit": UNIT}
             m2.close()
 
+    if rank == 0 and not args.no_extras and name == "c3":
+        extras["fp8_gemm_peak"] = fp8_gemm_peak(dev)
+
     if rank == 0 and not args.no_extras and args.precision != "fp32" and name == "c2":
         extras["batching"] = bench_batching(model, params, dev, stream)
         extras["serving"] = bench_serving(local)
@@ -461,7 +512,8 @@ def main():
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_step, "ms_per_step_stats": step_stats,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16" if args.precision != "fp32" else "f32", "data": "synthetic",
             "config": {"workload": describe(name), "rows_per_gpu": rows, "precision": args.precision,
                        "parallelism": f"replicas x{world} (rows sharded per GPU, no collective)",
