@@ -502,6 +502,18 @@ def main():
             extras[f"fused_{prec}"] = {"value": rows / (b0.elapsed_time(b1) / reps / 1e3), "unit": UNIT}
             m2.close()
 
+    if rank == 0 and not args.no_extras and name == "c2":
+        # a fresh process's first call (the serverless cold start), on the
+        # paper's model shape (14 inputs, n_d = n_a = 8, 3 steps)
+        extras["cold_start"] = {}
+        for mode in ("torch", "notorch"):
+            try:
+                out = subprocess.run([sys.executable, "-m", "paper_2510_19689_b300.cold_start", "c1", "1000",
+                                      "bf16x3", mode], cwd=ROOT, capture_output=True, text=True, timeout=600)
+                extras["cold_start"][mode] = json.loads(out.stdout.strip().splitlines()[-1])
+            except Exception as exc:
+                extras["cold_start"][mode] = {"unavailable": str(exc)[:200]}
+
     if rank == 0 and not args.no_extras and name == "c3":
         extras["fp8_gemm_peak"] = fp8_gemm_peak(dev)
 
