@@ -502,6 +502,22 @@ def main():
             extras[f"fused_{prec}"] = {"value": rows / (b0.elapsed_time(b1) / reps / 1e3), "unit": UNIT}
             m2.close()
 
+    if rank == 0 and not args.no_extras and args.precision != "fp32":
+        # audit statistics over the step's aggregate (mean, variance, top-5
+        # frequency per feature): the aggregate read twice plus once per row
+        ag0 = sets[0]["ag"]
+        for _ in range(3):
+            tabnet.mask_stats(ag0, 5, stream=stream)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(20):
+            tabnet.mask_stats(ag0, 5, stream=stream)
+        a1.record(stream)
+        a1.synchronize()
+        ms_stats = a0.elapsed_time(a1) / 20
+        extras["mask_stats"] = {"ms": ms_stats, "rows_per_s": rows / (ms_stats / 1e3), "k": 5,
+                                "aggregate_bytes": rows * d.n_feat * 4}
+
     if rank == 0 and not args.no_extras and name == "c2":
         # a fresh process's first call (the serverless cold start), on the
         # paper's model shape (14 inputs, n_d = n_a = 8, 3 steps)

@@ -331,6 +331,31 @@ void tabnet_destroy(tabnet_model* model);
 /* Static description of a status code. */
 const char* tabnet_status_string(int code);
 
+/* ---- audit statistics of aggregated masks (Sec. V-C: interpretability
+ * under load -- which features carry the decisions and whether their
+ * ranking holds).  Both read a [rows][d] float32 device array laid out as
+ * tabnet_forward's agg_mask output (any row-major [rows][d] float32 array
+ * works), need no model, run on `stream` and return once launched; they
+ * allocate their small scratch stream-ordered (cudaMallocAsync).  Errors:
+ * TABNET_ERR_ARG for a NULL input, rows < 1, d outside [1, 1024] or k
+ * outside [1, min(d, 32)]; TABNET_ERR_CUDA if an allocation or launch fails. */
+
+/* Per feature j over the rows (float32 device outputs, each may be NULL):
+ *   mean[j]      = (1/rows) sum_r agg[r][j]
+ *   var[j]       = (1/rows) sum_r (agg[r][j] - mean[j])^2   (population)
+ *   topk_frac[j] = fraction of rows whose k largest entries include j,
+ *                  equal entries ranked by the lower index first.
+ * Sums are compensated and combined in a fixed order (deterministic). */
+int tabnet_mask_stats(const float* agg, int64_t rows, int d, int k, float* mean, float* var,
+                      float* topk_frac, void* stream);
+
+/* Agreement of two aggregates' top-k feature sets, row by row (e.g. the same
+ * rows served alone and inside a mixed batch, or at two precisions):
+ *   *out = (1/(rows k)) sum_r |topk(agg_a[r]) intersect topk(agg_b[r])|
+ * with the tie rule above; out is one float32 in device memory. */
+int tabnet_topk_agreement(const float* agg_a, const float* agg_b, int64_t rows, int d, int k, float* out,
+                          void* stream);
+
 /* One-line reason for the last failing call made by this host thread
  * ("" when none).  The pointer stays valid until the thread's next call. */
 const char* tabnet_last_error(void);

@@ -37,7 +37,7 @@ EXPORTS = (
     "tabnet_reserve_segments", "tabnet_forward_segments_noalloc",
     "tabnet_server_create", "tabnet_server_submit", "tabnet_server_poll", "tabnet_server_wait",
     "tabnet_server_result", "tabnet_server_release", "tabnet_server_get_stats", "tabnet_server_reset_stats",
-    "tabnet_server_replay", "tabnet_server_destroy",
+    "tabnet_server_replay", "tabnet_server_destroy", "tabnet_mask_stats", "tabnet_topk_agreement",
 )
 #: fixed scratch capacity of tabnet_forward_segments_noalloc
 NOALLOC_MAX_SEGMENTS = 65536
@@ -129,6 +129,8 @@ def lib() -> ctypes.CDLL:
     L.tabnet_forward_segments_device.argtypes = [vp, vp, i32, vp]
     L.tabnet_reserve_segments.argtypes = [vp, i32]
     L.tabnet_forward_segments_noalloc.argtypes = [vp, vp, i32, vp]
+    L.tabnet_mask_stats.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp]
+    L.tabnet_topk_agreement.argtypes = [vp, vp, i64, i32, i32, vp, vp]
     L.tabnet_server_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
     L.tabnet_server_submit.argtypes = [vp, i32, vp, vp, i64, ctypes.POINTER(ctypes.c_uint64)]
     L.tabnet_server_poll.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), i32, ctypes.POINTER(ctypes.c_int)]
@@ -371,3 +373,28 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def mask_stats(agg, k: int, stream=None):
+    """Per-feature mean, variance and top-k frequency of a [rows, d] float32
+    CUDA tensor of aggregated masks (tabnet_mask_stats); returns three [d]
+    float32 CUDA tensors."""
+    import torch
+    rows, d = agg.shape
+    mean = torch.empty(d, dtype=torch.float32, device=agg.device)
+    var = torch.empty_like(mean)
+    frac = torch.empty_like(mean)
+    _check(lib().tabnet_mask_stats(_ptr(agg), rows, d, k, _ptr(mean), _ptr(var), _ptr(frac), _stream(stream)),
+           "tabnet_mask_stats")
+    return mean, var, frac
+
+
+def topk_agreement(agg_a, agg_b, k: int, stream=None):
+    """Mean row-wise overlap of the top-k feature sets of two [rows, d]
+    aggregates (tabnet_topk_agreement), as a one-element CUDA tensor."""
+    import torch
+    rows, d = agg_a.shape
+    out = torch.empty(1, dtype=torch.float32, device=agg_a.device)
+    _check(lib().tabnet_topk_agreement(_ptr(agg_a), _ptr(agg_b), rows, d, k, _ptr(out), _stream(stream)),
+           "tabnet_topk_agreement")
+    return out
