@@ -318,6 +318,20 @@ int tabnet_server_replay(tabnet_server* server, const tabnet_server_request* req
 /* Stop the engine, wait for the GPU, free everything. */
 void tabnet_server_destroy(tabnet_server* server);
 
+/* Preprocessing folded into the model (the upstream step of the paper's
+ * data pipeline, Sec. III-A): numeric column c is fed as
+ * (x_num[c] - num_mean[c]) * num_scale[c] (a fitted standard scaler:
+ * scale = 1 / std) and categorical column j as x_cat[j] - cat_base[j]
+ * (raw ordinal or label codes whose first category is cat_base[j]).  The
+ * scaler is folded into the input BN on the host (no work per row); the base
+ * is one subtraction in the gather.  Host arrays of n_num, n_num and n_cat
+ * entries; NULL means identity (mean 0, scale 1, base 0), and each call
+ * replaces the previous transform.  Synchronises the device first; no
+ * forward on this model may run concurrently with the call.  Errors: ARG
+ * (NULL model, a non-finite mean or scale), CUDA. */
+int tabnet_set_input_transform(tabnet_model* model, const float* num_mean, const float* num_scale,
+                               const int32_t* cat_base);
+
 /* Read and clear the handle's device status word (TABNET_STATUS_* bits) after
  * synchronising `stream`.  *status receives the bits; returns TABNET_OK when
  * no bit was set, TABNET_ERR_TIMEOUT when the timeout bit was set, else

@@ -38,6 +38,8 @@ struct ModelConsts {
     const float* emb;       // folded embedding tables, concatenated
     const int* cat_off;     // [n_cat] float offset of table j in emb
     const int* cat_card;    // [n_cat]
+    const int* cat_base;    // [n_cat] raw code of each column's index 0 (the caller's
+                            //      label/ordinal encoding, tabnet_set_input_transform)
     const int* feat_col;    // [d] first embedded column of feature j
     const int* feat_len;    // [d] embedded width of feature j
     const float* wf;        // [n_classes, n_d]

@@ -22,7 +22,7 @@ struct Arena {
 };
 
 struct ConstOffsets {
-    size_t s0, t0, emb, cat_off, cat_card, feat_col, feat_len, wf, bf;
+    size_t s0, t0, emb, cat_off, cat_card, cat_base, feat_col, feat_len, wf, bf;
 };
 
 // Launch shape of the tensor-core kernel (chosen by the host heuristics or

@@ -130,7 +130,7 @@ simt_forward_kernel(const SimtParams p, const float* __restrict__ x_num,
         } else {
             const int jc = j - m.n_num;
             const int len = m.feat_len[j];
-            const int idx = valid ? io.x_cat[jc] : 0;
+            const int idx = valid ? io.x_cat[jc] - m.cat_base[jc] : 0;
             const bool oob = idx < 0 || idx >= m.cat_card[jc];
             if (oob) atomicOr(m.status, TABNET_STATUS_CAT_OOB);
             const float* t = m.emb + m.cat_off[jc] + (size_t)(oob ? 0 : idx) * len;

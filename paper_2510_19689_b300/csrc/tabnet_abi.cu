@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -98,6 +99,8 @@ void build_consts(const HostModel& hm, Arena& a, ConstOffsets& o) {
     std::vector<int> card(hm.cat_card.begin(), hm.cat_card.end());
     if (card.empty()) card.push_back(1);
     o.cat_card = a.add(card.data(), card.size() * 4);
+    std::vector<int> cbase(card.size(), 0);
+    o.cat_base = a.add(cbase.data(), cbase.size() * 4);
     std::vector<int> fcol, flen;
     hm.feature_columns(fcol, flen);
     o.feat_col = a.add(fcol.data(), fcol.size() * 4);
@@ -118,6 +121,7 @@ void fill_consts(const HostModel& hm, const ConstOffsets& o, const uint8_t* base
     m.emb = (const float*)(base + o.emb);
     m.cat_off = (const int*)(base + o.cat_off);
     m.cat_card = (const int*)(base + o.cat_card);
+    m.cat_base = (const int*)(base + o.cat_base);
     m.feat_col = (const int*)(base + o.feat_col);
     m.feat_len = (const int*)(base + o.feat_len);
     m.wf = (const float*)(base + o.wf);
@@ -550,6 +554,37 @@ int tabnet_get_tile_config(const tabnet_model* m, int* nwg, int* n_slots, int* c
     if (nwg) *nwg = m->tc_launch_cfg.nwg;
     if (n_slots) *n_slots = m->tc_launch_cfg.n_slots;
     if (ctas_per_sm) *ctas_per_sm = m->tc_launch_cfg.ctas_per_sm;
+    return TABNET_OK;
+}
+
+int tabnet_set_input_transform(tabnet_model* m, const float* num_mean, const float* num_scale,
+                               const int32_t* cat_base) {
+    if (!m) return fail(TABNET_ERR_ARG, "null model");
+    const tabnet_dims& d = m->host.dims;
+    std::vector<float> s0, t0;
+    fold_bn(m->host.bn0, d.bn_eps, s0, t0);
+    // (x - mean) * scale through input BN s0 x + t0:  s0' = s0 scale, t0' = t0 - s0 scale mean
+    for (int c = 0; c < d.n_num; ++c) {
+        const double sc = num_scale ? (double)num_scale[c] : 1.0, mu = num_mean ? (double)num_mean[c] : 0.0;
+        if (!std::isfinite(sc) || !std::isfinite(mu)) return fail(TABNET_ERR_ARG, "non-finite scaler value");
+        const double s = (double)s0[c] * sc;
+        t0[c] = (float)((double)t0[c] - s * mu);
+        s0[c] = (float)s;
+    }
+    std::vector<int> cb(std::max(d.n_cat, 1), 0);
+    for (int j = 0; j < d.n_cat; ++j) cb[j] = cat_base ? cat_base[j] : 0;
+    DeviceGuard guard(m->device);
+    if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+    uint8_t* base = static_cast<uint8_t*>(m->d_arena);
+    cudaError_t e;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess ||
+        (d.n_num > 0 && (e = cudaMemcpy(base + m->consts_off.s0, s0.data(), sizeof(float) * d.n_num,
+                                        cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (d.n_num > 0 && (e = cudaMemcpy(base + m->consts_off.t0, t0.data(), sizeof(float) * d.n_num,
+                                        cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemcpy(base + m->consts_off.cat_base, cb.data(), sizeof(int) * cb.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "upload input transform");
     return TABNET_OK;
 }
 

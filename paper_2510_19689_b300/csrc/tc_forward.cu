@@ -486,7 +486,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 return fmaf(__ldg(m.s0 + c), x, __ldg(m.t0 + c));
             }
             if (ci.x >= 0) {
-                const int idx = valid ? __ldg(io.x_cat + ci.x) : 0;
+                const int idx = valid ? __ldg(io.x_cat + ci.x) - __ldg(m.cat_base + ci.x) : 0;
                 if (idx < 0 || idx >= __ldg(m.cat_card + ci.x)) {
                     if (check) atomicOr(m.status, TABNET_STATUS_CAT_OOB);
                     return __ldg(m.t0 + c);
@@ -536,7 +536,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             for (int jb = 0; jb < m.n_cat; jb += 32) {
                 const int j = jb + lane;
                 if (j < m.n_cat) {
-                    const int card = __ldg(m.cat_card + j);
+                    const int card = __ldg(m.cat_card + j), cbase = __ldg(m.cat_base + j);
                     const int c0 = __ldg(m.feat_col + m.n_num + j), len = __ldg(m.feat_len + m.n_num + j);
                     const float* tab = m.emb + __ldg(m.cat_off + j);
                     constexpr int G = RPW;  // every row of the warp's share in flight at once
@@ -546,7 +546,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 #pragma unroll
                         for (int i = 0; i < G; ++i) {
                             const int* cr = sRowC[i0 + i];
-                            iv[i] = cr ? __ldg(cr + j) : 0;
+                            iv[i] = cr ? __ldg(cr + j) - cbase : 0;
                         }
                         unsigned oob = 0;  // bit i: row i0 + i has an out-of-range index
 #pragma unroll

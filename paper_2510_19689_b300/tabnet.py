@@ -38,6 +38,7 @@ EXPORTS = (
     "tabnet_server_create", "tabnet_server_submit", "tabnet_server_poll", "tabnet_server_wait",
     "tabnet_server_result", "tabnet_server_release", "tabnet_server_get_stats", "tabnet_server_reset_stats",
     "tabnet_server_replay", "tabnet_server_destroy", "tabnet_mask_stats", "tabnet_topk_agreement",
+    "tabnet_set_input_transform",
 )
 #: fixed scratch capacity of tabnet_forward_segments_noalloc
 NOALLOC_MAX_SEGMENTS = 65536
@@ -130,6 +131,7 @@ def lib() -> ctypes.CDLL:
     L.tabnet_reserve_segments.argtypes = [vp, i32]
     L.tabnet_forward_segments_noalloc.argtypes = [vp, vp, i32, vp]
     L.tabnet_mask_stats.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp]
+    L.tabnet_set_input_transform.argtypes = [vp, vp, vp, vp]
     L.tabnet_topk_agreement.argtypes = [vp, vp, i64, i32, i32, vp, vp]
     L.tabnet_server_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
     L.tabnet_server_submit.argtypes = [vp, i32, vp, vp, i64, ctypes.POINTER(ctypes.c_uint64)]
@@ -257,6 +259,13 @@ class Model:
         _check(lib().tabnet_get_tile_config(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
                "tabnet_get_tile_config")
         return dict(nwg=a.value, n_slots=b.value, ctas_per_sm=c.value)
+
+    def set_input_transform(self, num_mean=None, num_scale=None, cat_base=None) -> None:
+        """Feed raw inputs: numeric (x - num_mean) * num_scale, categorical
+        x - cat_base (tabnet_set_input_transform); None = identity."""
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=t)
+                for a, t in ((num_mean, np.float32), (num_scale, np.float32), (cat_base, np.int32))]
+        _check(lib().tabnet_set_input_transform(self._h, *[_ptr(a) for a in arrs]), "tabnet_set_input_transform")
 
     def poll_status(self, stream=None) -> int:
         st = ctypes.c_uint32(0)
