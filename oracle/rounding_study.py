@@ -22,7 +22,9 @@ oracle is the effect of the operand rounding alone:
 * ``tf32``   both operands rounded to 11 significant bits;
 * ``e4m3``   weights scaled per output channel and FC inputs per row to
   amax / 448, rounded to FP8 E4M3 (3 stored mantissa bits, exponent down to
-  2^-6, subnormal steps of 2^-9, saturating at 448).
+  2^-6, subnormal steps of 2^-9, saturating at 448);
+* ``int8``   weights per output channel and FC inputs per row scaled to
+  amax / 127 and rounded to the nearest integer (symmetric INT8).
 
 These tables are why the library offers split-bf16 (it meets the stated
 bf16 tolerances) and no FP8 path (E4M3 operands move the sparsemax supports
@@ -34,7 +36,7 @@ import numpy as np
 
 from . import tabnet_oracle as O
 
-MODES = ("exact", "bf16", "bf16x3", "tf32", "e4m3")
+MODES = ("exact", "bf16", "bf16x3", "tf32", "e4m3", "int8")
 
 
 def round_significant(x, bits: int) -> np.ndarray:
@@ -59,6 +61,12 @@ def _e4m3_scaled(v: np.ndarray, axis: int) -> np.ndarray:
     return round_e4m3(v / scale) * scale
 
 
+def _int8_scaled(v: np.ndarray, axis: int) -> np.ndarray:
+    amax = np.abs(v).max(axis=axis, keepdims=True)
+    scale = np.where(amax > 0, amax / 127.0, 1.0)
+    return np.clip(np.rint(v / scale), -127, 127) * scale
+
+
 def _fc(x: np.ndarray, w, bn: dict, eps: float, mode: str) -> np.ndarray:
     """BN(x W^T) with W's BN scale folded and both operands rounded by `mode`."""
     s = np.asarray(bn["weight"], np.float64) / np.sqrt(np.asarray(bn["var"], np.float64) + eps)
@@ -76,6 +84,8 @@ def _fc(x: np.ndarray, w, bn: dict, eps: float, mode: str) -> np.ndarray:
         prod = round_significant(x, 11) @ round_significant(ws, 11).T
     elif mode == "e4m3":
         prod = _e4m3_scaled(x, axis=1) @ _e4m3_scaled(ws, axis=1).T
+    elif mode == "int8":
+        prod = _int8_scaled(x, axis=1) @ _int8_scaled(ws, axis=1).T
     else:
         raise ValueError(f"unknown rounding mode {mode!r}")
     return prod + t

@@ -83,3 +83,9 @@ def test_e4m3_moves_most_masks(name, rows):
     params, xn, xc, ref = _case(name, rows)
     e = R.error_summary(ref, R.forward_rounded(params, xn, xc, "e4m3"))
     assert e["mask_l1_mean"] > 5e-2
+
+
+def test_int8_moves_masks_too():
+    params, xn, xc, ref = _case("c2", 512)
+    e = R.error_summary(ref, R.forward_rounded(params, xn, xc, "int8"))
+    assert e["mask_l1_mean"] > 5e-2
