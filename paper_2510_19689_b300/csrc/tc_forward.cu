@@ -6,27 +6,36 @@
 // attentive FC, sparsemax, prior update, masked input and the step's feature
 // transformer, and finally the logits and the aggregated mask (TabNet as
 // deployed in Sec. IV-A; masks as returned per call, Sec. III-B).  Only the
-// inputs, the weights and the outputs touch global memory.
+// inputs, the weights and the outputs touch global memory.  CTAs are
+// persistent over tiles; a segmented launch finds each row's request.
 //
+//   * Tile start: the warps gather the tile's inputs together (each warp
+//     32 rows, all of their loads in flight per column), fold the input BN
+//     and keep f in shared memory; the next tile's rows are prefetched to L2.
 //   * Every FC is a 128 x n x K tcgen05.mma chain (M = 128 rows; n = 2N for a
 //     GLU layer, the padded mask width for the attentive layer) reading the
 //     activations (A) and the layer's weights (B) from shared memory in the
 //     128-byte-swizzled K-major layout and accumulating in fp32 in tensor
 //     memory (TMEM lane = row).  In split mode both operands are carried as
-//     hi + lo bf16 pairs and each K step issues hi*hi, hi*lo and lo*hi.
+//     hi + lo bf16 pairs and each K step issues hi*hi, hi*lo and lo*hi.  One
+//     phase loop walks a tile's layers, so there is one MMA issue site.
 //   * Weights stream from L2 through a ring of shared-memory slots filled by
 //     1-D bulk async copies (TMA engine), one 64-wide K block (hi or lo) per
 //     slot, pre-swizzled by the host.  Thread 0 issues copies and MMAs; each
-//     slot has a "full" barrier (copy landed) and an "empty" barrier (the
-//     MMAs that read it completed, via tcgen05.commit).
+//     slot has a "full" barrier (copy landed); a slot read by a layer's last
+//     K block is free once the accumulator barrier fires, earlier blocks'
+//     slots get their own "empty" commit.
 //   * Epilogue threads read the accumulator with tcgen05.ld (thread = row),
-//     apply the folded BN scale/shift, the GLU and the sqrt(0.5) residual
-//     (kept in fp32 registers), and write the next layer's A operand straight
-//     into shared memory.
+//     add the BN shift (the BN scale, -log2(e) for the gate and sqrt(1/2)
+//     for the residual are folded into the packed weights), apply the GLU
+//     and the residual (kept in fp32 registers), and write the next layer's
+//     A operand straight into shared memory.
 //   * Sparsemax runs in fp32, row per thread, by Michelot's fixed point on
 //     the threshold (the sort-free exact projection); the prior P lives in
 //     TMEM in fp32, the current mask in TMEM as fp16 pairs (read again only
-//     for the aggregate), the per-feature aggregate in shared memory.
+//     for the aggregate), the per-feature aggregate in TMEM or shared memory.
+//   * Masks and the aggregate leave through per-warp staging blocks as
+//     64-byte row pieces.
 //   * With NWG = 2 two warpgroups split the columns of each row and combine
 //     partial sums through shared memory.
 //
