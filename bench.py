@@ -287,7 +287,8 @@ def fp8_gemm_peak(dev, n=8192, reps=10):
         return {"value": None, "unavailable": str(exc)[:200]}
 
 
-def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), seconds=1.0):
+def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), seconds=1.0,
+                  streams_per_model=8, max_inflight_batches=32):
     """Poisson arrivals at each rate for `seconds`, request sizes
     floor(exp(U(0, ln 513))) in [1, 512] rows, the three model shapes
     resident (split-bf16), model chosen uniformly; the server's latency
@@ -298,7 +299,8 @@ def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), s
     models = [tabnet.Model(synth.to_blob(synth.make_params(synth.SPECS[n], synth.weight_seed(n))), "bf16x3",
                            device=dev_index) for n in names]
     pools = [synth.make_rows(n, 512, seed=5000 + i) for i, n in enumerate(names)]
-    srv = tabnet.Server(models, device_bytes=2 << 30)
+    srv = tabnet.Server(models, device_bytes=2 << 30, streams_per_model=streams_per_model,
+                        max_inflight_batches=max_inflight_batches)
     out = []
     for rate in rates:
         rng = np.random.default_rng(rate)

@@ -251,9 +251,10 @@ typedef struct tabnet_server tabnet_server;
 typedef struct {
     size_t device_bytes;       /* device memory for all rings (0: 1 GiB), split by bytes per row */
     int max_batch_rows;        /* rows per batch at most (0: 65536) */
-    int max_inflight_batches;  /* batches per model running on the GPU at once (0: 8); finished
+    int max_inflight_batches;  /* batches per model running on the GPU at once (0: 32); finished
                                   but unreleased results hold ring memory, not a slot */
-    int streams_per_model;     /* CUDA streams per model (0: 2) */
+    int streams_per_model;     /* CUDA streams per model (0: 8): small batches of one model
+                                  run side by side on different SMs */
 } tabnet_server_config;
 
 typedef struct {

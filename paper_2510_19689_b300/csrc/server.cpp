@@ -279,8 +279,8 @@ int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet
     if (!S) return tabnet::set_last_error(TABNET_ERR_OOM, "host allocation failed");
     S->cfg.device_bytes = cfg && cfg->device_bytes ? cfg->device_bytes : ((size_t)1 << 30);
     S->cfg.max_batch_rows = cfg && cfg->max_batch_rows > 0 ? cfg->max_batch_rows : 65536;
-    S->cfg.max_inflight_batches = cfg && cfg->max_inflight_batches > 0 ? cfg->max_inflight_batches : 8;
-    S->cfg.streams_per_model = cfg && cfg->streams_per_model > 0 ? cfg->streams_per_model : 2;
+    S->cfg.max_inflight_batches = cfg && cfg->max_inflight_batches > 0 ? cfg->max_inflight_batches : 32;
+    S->cfg.streams_per_model = cfg && cfg->streams_per_model > 0 ? cfg->streams_per_model : 8;
     S->device = models[0]->device;
     int prev = 0;
     cudaGetDevice(&prev);

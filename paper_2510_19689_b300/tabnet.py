@@ -302,8 +302,8 @@ class Server:
     """Continuous-batching request server over resident models
     (tabnet_server_*).  Inputs are numpy arrays kept alive until release."""
 
-    def __init__(self, models, device_bytes=1 << 30, max_batch_rows=65536, max_inflight_batches=8,
-                 streams_per_model=2):
+    def __init__(self, models, device_bytes=1 << 30, max_batch_rows=65536, max_inflight_batches=32,
+                 streams_per_model=8):
         self.models = list(models)
         arr = (ctypes.c_void_p * len(self.models))(*[m.handle for m in self.models])
         cfg = ServerConfig(device_bytes, max_batch_rows, max_inflight_batches, streams_per_model)
