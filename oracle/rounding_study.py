@@ -19,6 +19,9 @@ oracle is the effect of the operand rounding alone:
 * ``bf16x3`` each operand as hi + lo bfloat16 (lo = bf16(v - hi)) and the
   three products hi*hi + hi*lo + lo*hi accumulated, lo*lo dropped -- what
   three bf16 MMAs per K step compute;
+* ``bf16x2w`` / ``bf16x2a`` two of those products: the weight's lo term kept
+  (x_hi w_hi + x_hi w_lo) or the activation's (x_hi w_hi + x_lo w_hi) -- what
+  two MMAs per K step would compute;
 * ``tf32``   both operands rounded to 11 significant bits;
 * ``e4m3``   weights scaled per output channel and FC inputs per row to
   amax / 448, rounded to FP8 E4M3 (3 stored mantissa bits, exponent down to
@@ -26,8 +29,9 @@ oracle is the effect of the operand rounding alone:
 * ``int8``   weights per output channel and FC inputs per row scaled to
   amax / 127 and rounded to the nearest integer (symmetric INT8).
 
-These tables are why the library offers split-bf16 (it meets the stated
-bf16 tolerances) and no FP8 path (E4M3 operands move the sparsemax supports
+These tables are why the library offers split-bf16 with all three products
+(it meets the stated bf16 tolerances; neither two-product form does) and no
+FP8 path (E4M3 operands move the sparsemax supports
 of most rows).
 """
 from __future__ import annotations
@@ -36,7 +40,7 @@ import numpy as np
 
 from . import tabnet_oracle as O
 
-MODES = ("exact", "bf16", "bf16x3", "tf32", "e4m3", "int8")
+MODES = ("exact", "bf16", "bf16x3", "bf16x2w", "bf16x2a", "tf32", "e4m3", "int8")
 
 
 def round_significant(x, bits: int) -> np.ndarray:
@@ -76,10 +80,14 @@ def _fc(x: np.ndarray, w, bn: dict, eps: float, mode: str) -> np.ndarray:
         prod = x @ ws.T
     elif mode == "bf16":
         prod = round_significant(x, 8) @ round_significant(ws, 8).T
-    elif mode == "bf16x3":
+    elif mode in ("bf16x3", "bf16x2w", "bf16x2a"):
         xh, wh = round_significant(x, 8), round_significant(ws, 8)
         xl, wl = round_significant(x - xh, 8), round_significant(ws - wh, 8)
-        prod = xh @ wh.T + xh @ wl.T + xl @ wh.T
+        prod = xh @ wh.T
+        if mode != "bf16x2a":
+            prod = prod + xh @ wl.T
+        if mode != "bf16x2w":
+            prod = prod + xl @ wh.T
     elif mode == "tf32":
         prod = round_significant(x, 11) @ round_significant(ws, 11).T
     elif mode == "e4m3":

@@ -89,3 +89,26 @@ def test_int8_moves_masks_too():
     params, xn, xc, ref = _case("c2", 512)
     e = R.error_summary(ref, R.forward_rounded(params, xn, xc, "int8"))
     assert e["mask_l1_mean"] > 5e-2
+
+
+def test_two_product_forms_add_up_to_the_three_product_form():
+    """On one FC layer the products are separate terms: bf16x2w + bf16x2a -
+    bf16 (hi*hi counted once) must equal bf16x3 -- a dropped or doubled
+    term in any of the three modes fails this."""
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((40, 24))
+    w = rng.standard_normal((10, 24))
+    bn = dict(weight=rng.uniform(0.5, 2, 10), bias=rng.standard_normal(10), mean=rng.standard_normal(10),
+              var=rng.uniform(0.5, 2, 10))
+    f = {m: R._fc(x, w, bn, 1e-5, m) for m in ("bf16", "bf16x2w", "bf16x2a", "bf16x3")}
+    np.testing.assert_allclose(f["bf16x2w"] + f["bf16x2a"] - f["bf16"], f["bf16x3"], rtol=0, atol=1e-12)
+    assert np.abs(f["bf16x2w"] - f["bf16"]).max() > 0 and np.abs(f["bf16x2a"] - f["bf16"]).max() > 0
+
+
+@pytest.mark.parametrize("mode", ["bf16x2w", "bf16x2a"])
+def test_two_products_miss_the_mask_bar(mode):
+    """Dropping either correction product (two MMAs per K step instead of
+    three) moves some rows' masks past the stated 2e-2 bar."""
+    params, xn, xc, ref = _case("c2", 512)
+    e = R.error_summary(ref, R.forward_rounded(params, xn, xc, mode))
+    assert e["mask_l1_max"] > 2e-2
