@@ -206,8 +206,13 @@ int tabnet_forward_segments_noalloc(tabnet_model* model, const tabnet_segment* s
 
 /* Same computation with HOST buffers (pinned or pageable): the inputs are
  * copied into a device workspace owned by the handle, the forward runs, and
- * the outputs are copied back, all on `stream`; the call returns after the
- * stream has finished the copies (synchronous).  This is the paper's
+ * the outputs are copied back; the call returns after the copies have
+ * finished (synchronous).  A call with more than about 8 MB of outputs is
+ * split into row chunks (whole 128-row tiles) that run on four streams owned
+ * by the handle, so that input copies, kernels and output copies of
+ * different chunks overlap; those streams start after the work already
+ * queued on `stream`, and `stream` waits for them before the call returns.
+ * Every row's results are the same as in one tabnet_forward launch.  This is the paper's
  * function invocation (records in, predictions and masks out, Sec. III-B)
  * seen from a host caller.  Workspace grows on demand and is freed by
  * tabnet_destroy.  Not thread-safe per handle.  Errors: as tabnet_forward,

@@ -59,9 +59,14 @@ struct tabnet_model {
     size_t tc_off_chunks = 0, tc_off_epi = 0, tc_off_colinfo = 0, tc_off_colfeat = 0;
     std::vector<size_t> tc_chunk_off;          // arena offsets of the weight chunks, stream order
     std::vector<uint32_t> tc_chunk_bytes;
-    // host-buffer forward workspace
+    // host-buffer forward workspace, and the streams that pipeline its
+    // copies and launches over row chunks (created on first use)
     void* d_ws = nullptr;
     size_t ws_bytes = 0;
+    static constexpr int kHostStreams = 4;
+    cudaStream_t host_streams[kHostStreams] = {};
+    cudaEvent_t host_done[kHostStreams] = {};
+    cudaEvent_t host_start = nullptr;
     // segmented launches: device descriptors (host-staged calls) + prefix sums
     void* d_seg = nullptr;
     int seg_cap = 0;

@@ -399,11 +399,11 @@ int tabnet_forward_host(tabnet_model* m, const float* x_num, const int32_t* x_ca
     DeviceGuard guard(m->device);
     if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t b_num = (size_t)rows * d.n_num * 4, b_cat = (size_t)rows * d.n_cat * 4;
-    const size_t b_lg = (size_t)rows * d.n_classes * 4, b_mk = (size_t)rows * d.n_steps * d.d_emb * 4;
-    const size_t b_ag = (size_t)rows * d.n_feat * 4;
+    // bytes per row of each buffer
+    const size_t r_num = (size_t)d.n_num * 4, r_cat = (size_t)d.n_cat * 4, r_lg = (size_t)d.n_classes * 4;
+    const size_t r_mk = step_masks ? (size_t)d.n_steps * d.d_emb * 4 : 0, r_ag = agg_mask ? (size_t)d.n_feat * 4 : 0;
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t need = up(b_num) + up(b_cat) + up(b_lg) + (step_masks ? up(b_mk) : 0) + (agg_mask ? up(b_ag) : 0);
+    const size_t need = up(rows * r_num) + up(rows * r_cat) + up(rows * r_lg) + up(rows * r_mk) + up(rows * r_ag);
     cudaError_t e;
     if (need > m->ws_bytes) {
         if (m->d_ws) {
@@ -416,18 +416,77 @@ int tabnet_forward_host(tabnet_model* m, const float* x_num, const int32_t* x_ca
         m->ws_bytes = need;
     }
     uint8_t* w = static_cast<uint8_t*>(m->d_ws);
-    float* dn = (float*)w;            w += up(b_num);
-    int32_t* dc = (int32_t*)w;        w += up(b_cat);
-    float* dl = (float*)w;            w += up(b_lg);
-    float* dm = step_masks ? (float*)w : nullptr; if (step_masks) w += up(b_mk);
-    float* da = agg_mask ? (float*)w : nullptr;
-    if (b_num && (e = cudaMemcpyAsync(dn, x_num, b_num, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(e, "H2D x_num");
-    if (b_cat && (e = cudaMemcpyAsync(dc, x_cat, b_cat, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(e, "H2D x_cat");
-    rc = forward_impl(m, b_num ? dn : nullptr, b_cat ? dc : nullptr, rows, dl, dm, da, s);
-    if (rc != TABNET_OK) return rc;
-    if ((e = cudaMemcpyAsync(logits, dl, b_lg, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "D2H logits");
-    if (dm && (e = cudaMemcpyAsync(step_masks, dm, b_mk, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "D2H masks");
-    if (da && (e = cudaMemcpyAsync(agg_mask, da, b_ag, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "D2H agg");
+    uint8_t* dn = w;  w += up(rows * r_num);
+    uint8_t* dc = w;  w += up(rows * r_cat);
+    uint8_t* dl = w;  w += up(rows * r_lg);
+    uint8_t* dm = w;  w += up(rows * r_mk);
+    uint8_t* da = w;
+    // Row chunks of about 8 MB of outputs (whole 128-row tiles), each copied
+    // in, run and copied out on one of the handle's streams in turn: the
+    // input copy of a chunk, the kernels of others and the output copy of an
+    // earlier one overlap (the two copy directions and the SMs work at once).
+    const size_t r_out = r_lg + r_mk + r_ag;
+    int64_t chunk = (int64_t)((8u << 20) / r_out);
+    chunk = std::max<int64_t>(2048, chunk / 128 * 128);
+    const int64_t n_chunks = (rows + chunk - 1) / chunk;
+    const int n_str = (int)std::min<int64_t>(n_chunks, tabnet_model::kHostStreams);
+    if (n_chunks > 1 && !m->host_start) {
+        // all or nothing: host_start marks a complete set
+        for (int i = 0; i < tabnet_model::kHostStreams; ++i) {
+            if (!m->host_streams[i] &&
+                (e = cudaStreamCreateWithFlags(&m->host_streams[i], cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(e, "pipeline streams");
+            if (!m->host_done[i] && (e = cudaEventCreateWithFlags(&m->host_done[i], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "pipeline events");
+        }
+        if ((e = cudaEventCreateWithFlags(&m->host_start, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "pipeline events");
+    }
+    if (n_chunks > 1) {
+        // the chunks start after the work already on the caller's stream
+        if ((e = cudaEventRecord(m->host_start, s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        for (int i = 0; i < n_str; ++i)
+            if ((e = cudaStreamWaitEvent(m->host_streams[i], m->host_start, 0)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamWaitEvent");
+    }
+    auto h2d = [&](uint8_t* dst, const void* src, size_t b, cudaStream_t st) {
+        return b ? cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, st) : cudaSuccess;
+    };
+    auto d2h = [&](void* dst, const uint8_t* src, size_t b, cudaStream_t st) {
+        return b ? cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, st) : cudaSuccess;
+    };
+    for (int64_t c = 0; c < n_chunks; ++c) {
+        cudaStream_t st = n_chunks > 1 ? m->host_streams[c % n_str] : s;
+        const int64_t r0 = c * chunk, nr = std::min(chunk, rows - r0);
+        if ((e = h2d(dn + r0 * r_num, reinterpret_cast<const uint8_t*>(x_num) + r0 * r_num, nr * r_num, st)) !=
+            cudaSuccess)
+            return cuda_fail(e, "H2D x_num");
+        if ((e = h2d(dc + r0 * r_cat, reinterpret_cast<const uint8_t*>(x_cat) + r0 * r_cat, nr * r_cat, st)) !=
+            cudaSuccess)
+            return cuda_fail(e, "H2D x_cat");
+        rc = forward_impl(m, r_num ? reinterpret_cast<float*>(dn + r0 * r_num) : nullptr,
+                          r_cat ? reinterpret_cast<int32_t*>(dc + r0 * r_cat) : nullptr, nr,
+                          reinterpret_cast<float*>(dl + r0 * r_lg),
+                          step_masks ? reinterpret_cast<float*>(dm + r0 * r_mk) : nullptr,
+                          agg_mask ? reinterpret_cast<float*>(da + r0 * r_ag) : nullptr, st);
+        if (rc != TABNET_OK) return rc;
+        if ((e = d2h(reinterpret_cast<uint8_t*>(logits) + r0 * r_lg, dl + r0 * r_lg, nr * r_lg, st)) != cudaSuccess)
+            return cuda_fail(e, "D2H logits");
+        if (step_masks &&
+            (e = d2h(reinterpret_cast<uint8_t*>(step_masks) + r0 * r_mk, dm + r0 * r_mk, nr * r_mk, st)) != cudaSuccess)
+            return cuda_fail(e, "D2H masks");
+        if (agg_mask &&
+            (e = d2h(reinterpret_cast<uint8_t*>(agg_mask) + r0 * r_ag, da + r0 * r_ag, nr * r_ag, st)) != cudaSuccess)
+            return cuda_fail(e, "D2H agg");
+    }
+    if (n_chunks > 1) {
+        // the caller's stream continues after every chunk
+        for (int i = 0; i < n_str; ++i) {
+            if ((e = cudaEventRecord(m->host_done[i], m->host_streams[i])) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, m->host_done[i], 0)) != cudaSuccess)
+                return cuda_fail(e, "stream join");
+        }
+    }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return TABNET_OK;
 }
@@ -622,6 +681,11 @@ void tabnet_destroy(tabnet_model* m) {
         if (m->d_seg) cudaFree(m->d_seg);
         if (m->h_seg_stage) cudaFreeHost(m->h_seg_stage);
         if (m->seg_stage_done) cudaEventDestroy(m->seg_stage_done);
+        for (int i = 0; i < tabnet_model::kHostStreams; ++i) {
+            if (m->host_streams[i]) cudaStreamDestroy(m->host_streams[i]);
+            if (m->host_done[i]) cudaEventDestroy(m->host_done[i]);
+        }
+        if (m->host_start) cudaEventDestroy(m->host_start);
         tc_release(m);
     }
     delete m;
