@@ -449,6 +449,13 @@ int tabnet_forward_host(tabnet_model* m, const float* x_num, const int32_t* x_ca
             if ((e = cudaStreamWaitEvent(m->host_streams[i], m->host_start, 0)) != cudaSuccess)
                 return cuda_fail(e, "cudaStreamWaitEvent");
     }
+    // A failure part-way leaves no chunk running that a later call's copies
+    // into the workspace could overtake.
+    auto drain = [&](int rc_) {
+        if (n_chunks > 1)
+            for (int i = 0; i < n_str; ++i) cudaStreamSynchronize(m->host_streams[i]);
+        return rc_;
+    };
     auto h2d = [&](uint8_t* dst, const void* src, size_t b, cudaStream_t st) {
         return b ? cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, st) : cudaSuccess;
     };
@@ -460,31 +467,31 @@ int tabnet_forward_host(tabnet_model* m, const float* x_num, const int32_t* x_ca
         const int64_t r0 = c * chunk, nr = std::min(chunk, rows - r0);
         if ((e = h2d(dn + r0 * r_num, reinterpret_cast<const uint8_t*>(x_num) + r0 * r_num, nr * r_num, st)) !=
             cudaSuccess)
-            return cuda_fail(e, "H2D x_num");
+            return drain(cuda_fail(e, "H2D x_num"));
         if ((e = h2d(dc + r0 * r_cat, reinterpret_cast<const uint8_t*>(x_cat) + r0 * r_cat, nr * r_cat, st)) !=
             cudaSuccess)
-            return cuda_fail(e, "H2D x_cat");
+            return drain(cuda_fail(e, "H2D x_cat"));
         rc = forward_impl(m, r_num ? reinterpret_cast<float*>(dn + r0 * r_num) : nullptr,
                           r_cat ? reinterpret_cast<int32_t*>(dc + r0 * r_cat) : nullptr, nr,
                           reinterpret_cast<float*>(dl + r0 * r_lg),
                           step_masks ? reinterpret_cast<float*>(dm + r0 * r_mk) : nullptr,
                           agg_mask ? reinterpret_cast<float*>(da + r0 * r_ag) : nullptr, st);
-        if (rc != TABNET_OK) return rc;
+        if (rc != TABNET_OK) return drain(rc);
         if ((e = d2h(reinterpret_cast<uint8_t*>(logits) + r0 * r_lg, dl + r0 * r_lg, nr * r_lg, st)) != cudaSuccess)
-            return cuda_fail(e, "D2H logits");
+            return drain(cuda_fail(e, "D2H logits"));
         if (step_masks &&
             (e = d2h(reinterpret_cast<uint8_t*>(step_masks) + r0 * r_mk, dm + r0 * r_mk, nr * r_mk, st)) != cudaSuccess)
-            return cuda_fail(e, "D2H masks");
+            return drain(cuda_fail(e, "D2H masks"));
         if (agg_mask &&
             (e = d2h(reinterpret_cast<uint8_t*>(agg_mask) + r0 * r_ag, da + r0 * r_ag, nr * r_ag, st)) != cudaSuccess)
-            return cuda_fail(e, "D2H agg");
+            return drain(cuda_fail(e, "D2H agg"));
     }
     if (n_chunks > 1) {
         // the caller's stream continues after every chunk
         for (int i = 0; i < n_str; ++i) {
             if ((e = cudaEventRecord(m->host_done[i], m->host_streams[i])) != cudaSuccess ||
                 (e = cudaStreamWaitEvent(s, m->host_done[i], 0)) != cudaSuccess)
-                return cuda_fail(e, "stream join");
+                return drain(cuda_fail(e, "stream join"));
         }
     }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");

@@ -137,13 +137,31 @@ def test_optional_outputs_and_zero_rows(tabnet_mod, precision):
     m.close()
 
 
+# The 100-input model's layout with two steps: its embedded width (160
+# columns), A operand, weight ring and shared-memory aggregate leave no room to
+# stage the inputs, so the kernel gathers f from global memory at tile start
+# and at every step, and the out-of-range check there is exercised too.
+WIDE_UNSTAGED = synth.TabNetSpec(n_num=80, cat_card=synth.SPECS["c3"].cat_card, cat_emb_dim=(4,) * 20, n_d=64,
+                                 n_a=64, n_steps=2, gamma=1.3, n_classes=3)
+
+
 @pytest.mark.parametrize("precision", PRECISIONS)
-def test_out_of_range_category_sets_status(tabnet_mod, precision):
-    params = synth.make_params(synth.SPECS["c1"], 6)
-    x_num, x_cat = synth.make_rows("c1", 64)
+@pytest.mark.parametrize("model", ["c1", "wide_unstaged"])
+def test_out_of_range_category_sets_status(tabnet_mod, precision, model):
+    if model == "c1":
+        params = synth.make_params(synth.SPECS["c1"], 6)
+        x_num, x_cat = synth.make_rows("c1", 64)
+    else:
+        if precision == "fp32":
+            pytest.skip("the fp32 path stages nothing; covered by the c1 case")
+        params = synth.make_params(WIDE_UNSTAGED, 7, bn_affine="random")
+        rng = np.random.default_rng(70)
+        x_num = rng.lognormal(0.0, 1.0, size=(300, WIDE_UNSTAGED.n_num)).astype(np.float32)
+        x_cat = np.stack([rng.integers(0, c, size=300) for c in WIDE_UNSTAGED.cat_card], axis=1).astype(np.int32)
     bad = x_cat.copy()
-    bad[5, 2] = 1000
+    bad[5, -1] = 100000
     bad[9, 0] = -3
+    bad[len(bad) - 1, 1] = -1
     gpu, status = run_gpu(tabnet_mod, synth.to_blob(params), precision, x_num, bad)
     assert status & 0x1
     # the reference: the same rows with a zero embedding row for those entries
