@@ -239,3 +239,29 @@ def test_fp8_is_refused(tabnet_mod):
     with pytest.raises(tabnet_mod.TabnetError) as e:
         tabnet_mod.Model(synth.to_blob(params), "fp8")
     assert e.value.code == -6 and "E4M3" in str(e.value)
+
+
+def test_outputs_past_the_int32_element_range(tabnet_mod):
+    """1,400,000 rows of the 100-input model in one launch: the step masks
+    hold 2.24e9 elements, past 2^31, so every row-offset product must be
+    64-bit.  Rows on both sides of mask element 2^31 and the last rows match
+    the oracle; every row's masks sum to 1 (checked on the device)."""
+    rows = 1_400_000
+    spec = synth.SPECS["c3"]
+    params = synth.make_params(spec, synth.weight_seed("c3"))
+    x_num, x_cat = synth.make_rows("c3", rows, seed=4242)
+    m = tabnet_mod.Model(synth.to_blob(params), "bf16x3")
+    dev = torch.device("cuda", 0)
+    lg, mk, ag = m.run(torch.from_numpy(x_num).to(dev), torch.from_numpy(x_cat).to(dev))
+    torch.cuda.synchronize()
+    assert m.poll_status() == 0
+    m.close()
+    per_row = spec.n_steps * spec.d_emb
+    assert rows * per_row > 2 ** 31
+    assert float((mk.sum(dim=2) - 1).abs().max()) <= 5e-5
+    edge = 2 ** 31 // per_row
+    idx = np.array([0, edge - 1, edge, edge + 1, rows - 2, rows - 1])
+    it = torch.from_numpy(idx).to(dev)
+    sample = (lg[it].cpu().numpy(), mk[it].cpu().numpy(), ag[it].cpu().numpy())
+    del lg, mk, ag
+    check("bf16x3", sample, O.forward(params, x_num[idx], x_cat[idx]))
