@@ -386,17 +386,28 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             PH_MARK(9);
             acc_outstanding = true;
             if (!ok) *sAbort = 1;
-
-            // Only this thread waits on the accumulator barrier; the others
-            // park on the CTA barrier below, which costs no issue slots.
-            const bool got = ptx::mbar_wait(bar_acc, acc_phase, kWaitLimit);
-            PH_MARK(10);
-            if (got) {
-                acc_outstanding = false;
-            } else {
+        }
+        __syncwarp();
+        // With two warpgroups every thread waits for the accumulator itself,
+        // suspended in the barrier's try-wait (no issue slots spent), so each
+        // warp's epilogue starts as soon as the MMAs complete rather than
+        // after thread 0 has woken, refilled the ring and released a 256-thread
+        // barrier (+2 % on the 100-input model).  With one warpgroup thread 0
+        // waits alone and the others park on the CTA barrier (the all-thread
+        // wait measured 1 % slower there).  No thread can fall a phase behind:
+        // the next commit needs every thread at the next layer's CTA barrier.
+        constexpr bool kAllWait = NWG == 2;
+        bool got = true;
+        if (kAllWait || tid == 0) {
+            got = ptx::mbar_wait(bar_acc, acc_phase, kWaitLimit);
+            if (!got) {
                 *sAbort = 1;
                 note_timeout(m.status, 2, (unsigned)lc);
             }
+        }
+        PH_MARK(10);
+        if (tid == 0) {
+            if (got) acc_outstanding = false;
             // every MMA so far has completed: refill the free slots
             if (!*sAbort)
                 while (g_issue < total_chunks && g_issue < g_cons + S)
@@ -405,7 +416,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         }
         acc_phase ^= 1;
         ++lc;
-        __syncthreads();
+        if constexpr (!kAllWait) __syncthreads();
         ptx::tc_fence_after();
         PH_MARK(1);
         return true;
