@@ -226,6 +226,10 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.sm.bar);
     const int S = p.n_slots;
     volatile uint32_t* sTmem = reinterpret_cast<volatile uint32_t*>(bars + 2 * S + 1);
+    // Stop flags, one per layer parity: a thread that finds during layer L
+    // that the CTA has to stop sets the flag of layer L + 1, which every
+    // thread reads after that layer's CTA barrier -- never the flag of the
+    // layer whose flag other threads may still be reading.
     volatile int* sAbort = reinterpret_cast<volatile int*>(bars + 2 * S + 2);
     const uint32_t bar_full = ptx::smem_u32(bars);
     const uint32_t bar_empty = ptx::smem_u32(bars + S);
@@ -236,7 +240,8 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 
     if (tid == 0) {
         for (int s = 0; s < 2 * S + 1; ++s) ptx::mbar_init(bar_full + 8 * s, 1);
-        *sAbort = 0;
+        sAbort[0] = 0;
+        sAbort[1] = 0;
         ptx::fence_mbar_init();
     }
     if (warp == 0) {
@@ -321,7 +326,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         ptx::fence_proxy_async();
         ptx::tc_fence_before();
         __syncthreads();
-        if (*sAbort) return false;
+        if (sAbort[lc & 1]) return false;
         if (tid == 0) {
             ptx::tc_fence_after();
             int kk = 0;
@@ -385,7 +390,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             ptx::mma_commit(bar_acc);
             PH_MARK(9);
             acc_outstanding = true;
-            if (!ok) *sAbort = 1;
+            if (!ok) sAbort[(lc + 1) & 1] = 1;
         }
         __syncwarp();
         // With two warpgroups every thread waits for the accumulator itself,
@@ -401,7 +406,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         if (kAllWait || tid == 0) {
             got = ptx::mbar_wait(bar_acc, acc_phase, kWaitLimit);
             if (!got) {
-                *sAbort = 1;
+                sAbort[(lc + 1) & 1] = 1;
                 note_timeout(m.status, 2, (unsigned)lc);
             }
         }
@@ -409,9 +414,9 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         if (tid == 0) {
             if (got) acc_outstanding = false;
             // every MMA so far has completed: refill the free slots
-            if (!*sAbort)
+            if (!sAbort[(lc + 1) & 1])
                 while (g_issue < total_chunks && g_issue < g_cons + S)
-                    if (!issue_next()) { *sAbort = 1; break; }
+                    if (!issue_next()) { sAbort[(lc + 1) & 1] = 1; break; }
             PH_MARK(11);
         }
         acc_phase ^= 1;
@@ -422,6 +427,14 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         return true;
     };
 
+    // With two warpgroups, warps w and w + 4 hold the same 32 rows (the same
+    // TMEM lanes) and are the only threads that exchange row data: they meet
+    // at a barrier of their own (ids 1..4, 64 threads), so the other pairs
+    // run on.
+    auto pair_sync = [&]() {
+        if constexpr (NWG == 2) ptx::named_bar_sync(1 + (warp & 3), 64);
+    };
+
     // Sum of (a, b) over the warpgroups sharing a row, same order everywhere.
     auto xsum = [&](float a, float b) -> float2 {
         if constexpr (NWG == 1) {
@@ -429,7 +442,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         } else {
             float2* slot = sX + (xc & 1) * 256;
             slot[wg * 128 + lt] = make_float2(a, b);
-            ptx::named_bar_sync(1, THREADS);
+            pair_sync();
             const float2 o = slot[(wg ^ 1) * 128 + lt];
             ++xc;
             return wg == 0 ? make_float2(a + o.x, b + o.y) : make_float2(o.x + a, o.y + b);
@@ -463,7 +476,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         } else {
             float2* slot = sX + (xc & 1) * 256;
             slot[wg * 128 + lt] = make_float2(a, b);
-            ptx::named_bar_sync(1, THREADS);
+            pair_sync();
             const float2 o = slot[(wg ^ 1) * 128 + lt];
             ++xc;
             return make_float2(wg == 0 ? a + o.x : o.x + a, fmaxf(b, o.y));
@@ -613,8 +626,13 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 ptx::tmem_st16(t_agg + ch * 16, zeros);
             }
         }
-        if (!agg_tmem)
+        if (!agg_tmem) {
+            // the partner warp may still be reading the last tile's aggregate
+            // of these rows (it stages 16-feature blocks, not this thread's
+            // interleaved subset)
+            pair_sync();
             for (int j = wg; j < m.d; j += NWG) sAgg[j * 128 + lt] = 0.f;
+        }
         ptx::tmem_wait_st();
         PH_MARK(0);
         float lacc[kMaxClasses];
@@ -705,8 +723,9 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 bool done = false;
                 // Rows converge after different numbers of passes, but TMEM
                 // loads and the warpgroup exchange are collective: every thread
-                // runs every pass until the last row of its warp (CTA) has
-                // converged; a converged row keeps its threshold.
+                // runs every pass until the last row of its warp (of its warp
+                // pair, with two warpgroups) has converged; a converged row
+                // keeps its threshold.
 #pragma unroll 1
                 for (int it = 0; it < de; ++it) {
                     float ss = 0.f, cnt = 0.f;
@@ -742,11 +761,9 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                             tau = (t.x - 1.f) / t.y;
                         }
                     }
-                    if constexpr (NWG == 1) {
-                        if (!__any_sync(0xffffffffu, !done)) break;
-                    } else {
-                        if (!ptx::named_bar_or(2, THREADS, !done)) break;
-                    }
+                    // the two warps holding these rows see the same totals,
+                    // hence the same flags, and leave together
+                    if (!__any_sync(0xffffffffu, !done)) break;
                 }
                 TC_TRACE(128 + tid / 32, 4000 + lc);
                 PH_MARK(2);
@@ -1000,7 +1017,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 }
             }
         } else {
-            if constexpr (NWG > 1) ptx::named_bar_sync(2, THREADS);  // every aggregate update is in shared memory
+            pair_sync();  // both warpgroups' aggregate updates of these rows are in shared memory
             float tot = 0.f;
             for (int j = wg; j < m.d; j += NWG) tot += sAgg[j * 128 + lt];
             tot = xsum(tot, 0.f).x;
