@@ -27,7 +27,9 @@ oracle is the effect of the operand rounding alone:
   amax / 448, rounded to FP8 E4M3 (3 stored mantissa bits, exponent down to
   2^-6, subnormal steps of 2^-9, saturating at 448);
 * ``int8``   weights per output channel and FC inputs per row scaled to
-  amax / 127 and rounded to the nearest integer (symmetric INT8).
+  amax / 127 and rounded to the nearest integer (symmetric INT8);
+* ``int8w``  weights alone as in ``int8``, FC inputs exact (a weight-only
+  INT8 variant, the best any INT8-weight kernel could do).
 
 These tables are why the library offers split-bf16 with all three products
 (it meets the stated bf16 tolerances; neither two-product form does) and no
@@ -40,7 +42,7 @@ import numpy as np
 
 from . import tabnet_oracle as O
 
-MODES = ("exact", "bf16", "bf16x3", "bf16x2w", "bf16x2a", "tf32", "e4m3", "int8")
+MODES = ("exact", "bf16", "bf16x3", "bf16x2w", "bf16x2a", "tf32", "e4m3", "int8", "int8w")
 
 
 def round_significant(x, bits: int) -> np.ndarray:
@@ -94,6 +96,8 @@ def _fc(x: np.ndarray, w, bn: dict, eps: float, mode: str) -> np.ndarray:
         prod = _e4m3_scaled(x, axis=1) @ _e4m3_scaled(ws, axis=1).T
     elif mode == "int8":
         prod = _int8_scaled(x, axis=1) @ _int8_scaled(ws, axis=1).T
+    elif mode == "int8w":
+        prod = x @ _int8_scaled(ws, axis=1).T
     else:
         raise ValueError(f"unknown rounding mode {mode!r}")
     return prod + t

@@ -112,3 +112,19 @@ def test_two_products_miss_the_mask_bar(mode):
     params, xn, xc, ref = _case("c2", 512)
     e = R.error_summary(ref, R.forward_rounded(params, xn, xc, mode))
     assert e["mask_l1_max"] > 2e-2
+
+
+def test_weight_only_int8_moves_masks():
+    """INT8 weights with exact activations -- the best any INT8-weight kernel
+    could do -- still move the masks past the bar (mean L1 above 5e-2)."""
+    params, xn, xc, ref = _case("c2", 512)
+    e = R.error_summary(ref, R.forward_rounded(params, xn, xc, "int8w"))
+    assert e["mask_l1_mean"] > 5e-2 and e["mask_l1_max"] > 2e-2
+
+
+def test_int8_weight_rounding_is_symmetric_per_channel():
+    w = np.array([[1.0, -0.5, 0.25], [0.0, 0.0, 0.0], [3.0, 1.0, -2.9]])
+    q = R._int8_scaled(w, axis=1)
+    np.testing.assert_allclose(q[0], np.array([127, -64, 32]) / 127.0)   # -63.5 -> -64 (ties to even)
+    np.testing.assert_array_equal(q[1], 0.0)                             # an all-zero channel stays zero
+    np.testing.assert_allclose(q[2], np.array([127, 42, -123]) * 3.0 / 127.0)
