@@ -258,8 +258,8 @@ typedef struct {
     int max_batch_rows;        /* rows per batch at most (0: 65536) */
     int max_inflight_batches;  /* batches per model running on the GPU at once (0: 32); finished
                                   but unreleased results hold ring memory, not a slot */
-    int streams_per_model;     /* CUDA streams per model (0: 8): small batches of one model
-                                  run side by side on different SMs */
+    int streams_per_model;     /* CUDA streams per model (0: 8, at most 64): small batches of
+                                  one model run side by side on different SMs */
 } tabnet_server_config;
 
 typedef struct {

@@ -106,6 +106,7 @@ struct tabnet_server {
     std::atomic<bool> stop{false};
     int device = 0;
     int error = TABNET_OK;
+    std::vector<cudaEvent_t> free_events;  // completion events of freed batches, reused (engine thread only)
 };
 
 namespace {
@@ -148,12 +149,22 @@ void engine_loop(tabnet_server* S) {
     std::vector<Request*> take;
     while (!S->stop.load(std::memory_order_relaxed)) {
         bool did = false;
-        // 1. completions
+        // 1. completions: batches of one stream finish in order, batches of
+        // different streams in any order, so each stream's oldest unfinished
+        // batch is asked and a stream is skipped once one of its batches is
+        // still running (a short batch is not held behind a long one on
+        // another stream)
         for (auto& mc : S->models) {
+            uint64_t blocked = 0;  // bit i: stream i has a batch still running
             for (Batch* b : mc.inflight) {
                 if (b->complete) continue;
+                const uint64_t bit = 1ull << (b->stream_idx & 63);
+                if (blocked & bit) continue;
                 const cudaError_t q = cudaEventQuery(b->done);
-                if (q == cudaErrorNotReady) break;  // later batches of this stream order come later
+                if (q == cudaErrorNotReady) {
+                    blocked |= bit;
+                    continue;
+                }
                 const auto now = Clock::now();
                 std::lock_guard<std::mutex> lk(S->mu);
                 b->complete = true;
@@ -175,7 +186,7 @@ void engine_loop(tabnet_server* S) {
                    mc.inflight.front()->released == (int)mc.inflight.front()->tickets.size()) {
                 Batch* b = mc.inflight.front();
                 ring_free_front(mc);
-                cudaEventDestroy(b->done);
+                S->free_events.push_back(b->done);
                 delete b;
                 did = true;
             }
@@ -243,7 +254,12 @@ void engine_loop(tabnet_server* S) {
             mc.next_stream = (mc.next_stream + 1) % (int)mc.streams.size();
             cudaStream_t st = mc.streams[b->stream_idx];
             uint8_t* dv = mc.dev + off;
-            cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+            if (!S->free_events.empty()) {
+                b->done = S->free_events.back();
+                S->free_events.pop_back();
+            } else {
+                cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+            }
             cudaMemcpyAsync(dv, h, in_bytes, cudaMemcpyHostToDevice, st);
             int rc = tabnet_forward(mc.model, d.n_num ? (const float*)(dv + b->in_num) : nullptr,
                                     d.n_cat ? (const int32_t*)(dv + b->in_cat) : nullptr, rows,
@@ -280,7 +296,7 @@ int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet
     S->cfg.device_bytes = cfg && cfg->device_bytes ? cfg->device_bytes : ((size_t)1 << 30);
     S->cfg.max_batch_rows = cfg && cfg->max_batch_rows > 0 ? cfg->max_batch_rows : 65536;
     S->cfg.max_inflight_batches = cfg && cfg->max_inflight_batches > 0 ? cfg->max_inflight_batches : 32;
-    S->cfg.streams_per_model = cfg && cfg->streams_per_model > 0 ? cfg->streams_per_model : 8;
+    S->cfg.streams_per_model = cfg && cfg->streams_per_model > 0 ? std::min(cfg->streams_per_model, 64) : 8;
     S->device = models[0]->device;
     int prev = 0;
     cudaGetDevice(&prev);
@@ -453,11 +469,14 @@ int tabnet_server_replay(tabnet_server* S, const tabnet_server_request* reqs, in
     if (!S || (n > 0 && !reqs) || n < 0) return tabnet::set_last_error(TABNET_ERR_ARG, "bad arguments");
     const auto t0 = Clock::now();
     std::vector<uint64_t> done(1024);
-    std::deque<uint64_t> outstanding;
+    // Release finished requests while waiting for the next arrival, at most
+    // every 20 us: polling on every spin would contend for the engine's lock.
+    auto last_poll = t0;
     for (int i = 0; i < n; ++i) {
         const auto due = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(reqs[i].arrival_s));
-        while (Clock::now() < due) {
-            if (release) {  // release finished requests while waiting for the next arrival
+        for (auto now = Clock::now(); now < due; now = Clock::now()) {
+            if (release && now - last_poll >= std::chrono::microseconds(20)) {
+                last_poll = now;
                 int k = 0;
                 tabnet_server_poll(S, done.data(), (int)done.size(), &k);
                 for (int j = 0; j < k; ++j) tabnet_server_release(S, done[j]);
@@ -503,6 +522,7 @@ void tabnet_server_destroy(tabnet_server* S) {
         if (mc.dev) cudaFree(mc.dev);
         if (mc.host) cudaFreeHost(mc.host);
     }
+    for (cudaEvent_t e : S->free_events) cudaEventDestroy(e);
     for (auto& kv : S->reqs) {
         bool pending = false;
         for (auto& mc : S->models)
