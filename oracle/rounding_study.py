@@ -23,6 +23,12 @@ oracle is the effect of the operand rounding alone:
   (x_hi w_hi + x_hi w_lo) or the activation's (x_hi w_hi + x_lo w_hi) -- what
   two MMAs per K step would compute;
 * ``tf32``   both operands rounded to 11 significant bits;
+* ``bf16x6`` each operand as three bfloat16 parts (hi, mid = bf16(v - hi),
+  lo = bf16(v - hi - mid)) and the six products whose parts' significance
+  sums reach 2^-24 (hi hi, hi mid, mid hi, hi lo, mid mid, lo hi);
+* ``tf32x3`` each operand as hi + lo in 11-bit significands, three products
+  as in ``bf16x3`` -- with ``bf16x6``, the candidates for a tensor-core mode
+  at float32 accuracy;
 * ``e4m3``   weights scaled per output channel and FC inputs per row to
   amax / 448, rounded to FP8 E4M3 (3 stored mantissa bits, exponent down to
   2^-6, subnormal steps of 2^-9, saturating at 448);
@@ -42,7 +48,7 @@ import numpy as np
 
 from . import tabnet_oracle as O
 
-MODES = ("exact", "bf16", "bf16x3", "bf16x2w", "bf16x2a", "tf32", "e4m3", "int8", "int8w")
+MODES = ("exact", "bf16", "bf16x3", "bf16x2w", "bf16x2a", "tf32", "bf16x6", "tf32x3", "e4m3", "int8", "int8w")
 
 
 def round_significant(x, bits: int) -> np.ndarray:
@@ -59,6 +65,16 @@ def round_e4m3(x) -> np.ndarray:
     binade = np.maximum(e - 1, -6)        # subnormals share the 2^-6 binade's spacing
     step = np.ldexp(1.0, binade - 3)
     return np.sign(x) * np.minimum(np.rint(a / step) * step, 448.0)
+
+
+def _parts(v: np.ndarray, bits: int, n: int) -> list:
+    """v as n terms of `bits` significant bits: each the rounded remainder."""
+    out, rem = [], np.asarray(v, np.float64)
+    for _ in range(n):
+        t = round_significant(rem, bits)
+        out.append(t)
+        rem = rem - t
+    return out
 
 
 def _e4m3_scaled(v: np.ndarray, axis: int) -> np.ndarray:
@@ -92,6 +108,12 @@ def _fc(x: np.ndarray, w, bn: dict, eps: float, mode: str) -> np.ndarray:
             prod = prod + xl @ wh.T
     elif mode == "tf32":
         prod = round_significant(x, 11) @ round_significant(ws, 11).T
+    elif mode == "bf16x6":
+        xs, wv = _parts(x, 8, 3), _parts(ws, 8, 3)
+        prod = sum(xs[i] @ wv[j].T for i, j in ((0, 0), (0, 1), (1, 0), (0, 2), (1, 1), (2, 0)))
+    elif mode == "tf32x3":
+        xs, wv = _parts(x, 11, 2), _parts(ws, 11, 2)
+        prod = xs[0] @ wv[0].T + xs[0] @ wv[1].T + xs[1] @ wv[0].T
     elif mode == "e4m3":
         prod = _e4m3_scaled(x, axis=1) @ _e4m3_scaled(ws, axis=1).T
     elif mode == "int8":

@@ -128,3 +128,31 @@ def test_int8_weight_rounding_is_symmetric_per_channel():
     np.testing.assert_allclose(q[0], np.array([127, -64, 32]) / 127.0)   # -63.5 -> -64 (ties to even)
     np.testing.assert_array_equal(q[1], 0.0)                             # an all-zero channel stays zero
     np.testing.assert_allclose(q[2], np.array([127, 42, -123]) * 3.0 / 127.0)
+
+
+def test_three_part_split_is_exact_to_24_bits():
+    """hi + mid + lo of the bf16x6 split reproduces a float32 value exactly
+    (3 x 8 significant bits cover float32's 24); two parts leave the third."""
+    rng = np.random.default_rng(4)
+    x = (rng.standard_normal(5000) * np.exp(rng.uniform(-10, 10, 5000))).astype(np.float32).astype(np.float64)
+    p3 = R._parts(x, 8, 3)
+    np.testing.assert_array_equal(p3[0] + p3[1] + p3[2], x)
+    p2 = R._parts(x, 8, 2)
+    np.testing.assert_array_equal(x - (p2[0] + p2[1]), p3[2])
+
+
+@pytest.mark.parametrize("mode", ["bf16x6", "tf32x3"])
+@pytest.mark.parametrize("name,rows", [("c1", 512), ("c2", 512)])
+def test_six_bf16_or_three_tf32_products_meet_the_fp32_bar(mode, name, rows):
+    """Operand rounding alone of the tensor-core modes that would give
+    float32 results: logits within 1e-5 relative, masks within the fp32
+    tests' 5e-4 -- while split-bf16 misses the logit bar on the 35-input
+    model."""
+    params, xn, xc, ref = _case(name, rows)
+    got = R.forward_rounded(params, xn, xc, mode)
+    assert (np.abs(got[0] - ref[0]) / np.maximum(np.abs(ref[0]), 1)).max() <= 1e-5
+    e = R.error_summary(ref, got)
+    assert e["mask_l1_max"] <= 5e-4 and e["agg_l1_max"] <= 5e-4
+    if name == "c2":
+        b = R.forward_rounded(params, xn, xc, "bf16x3")
+        assert (np.abs(b[0] - ref[0]) / np.maximum(np.abs(ref[0]), 1)).max() > 1e-5
