@@ -69,11 +69,18 @@ typedef enum {
                              the 14-, 35- and 100-input models), so no kernel is
                              built; tabnet_create returns
                              TABNET_ERR_UNSUPPORTED_DIMS for it */
-    TABNET_BF16X3 = 3     /* split bf16 on the same tensor cores: each operand
+    TABNET_BF16X3 = 3,    /* split bf16 on the same tensor cores: each operand
                              carried as hi + lo bf16 (lo = bf16(x - hi)), three
                              bf16 MMAs per K step (hi*hi + hi*lo + lo*hi) into
                              one fp32 accumulator, accurate sigmoid; about
                              16 significant bits per operand */
+    TABNET_BF16X6 = 4     /* float32-accurate FCs on the tensor cores: each
+                             operand as hi + mid + lo bf16 (exact for float32
+                             values), six bf16 MMAs per K step (every product
+                             down to 2^-16 of hi*hi) into one fp32 accumulator;
+                             meets the float32 tolerances.  Needs
+                             n_d + n_a <= 64 (TABNET_ERR_UNSUPPORTED_DIMS
+                             otherwise) */
 } tabnet_precision;
 
 /* Model shape, as read from a blob. */

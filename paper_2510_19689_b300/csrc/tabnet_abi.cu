@@ -274,7 +274,7 @@ int tabnet_blob_inspect(const void* blob, size_t blob_bytes, tabnet_dims* out) {
 int tabnet_create(const void* blob, size_t blob_bytes, int precision, int device, tabnet_model** out) {
     if (!blob || !out) return fail(TABNET_ERR_ARG, "null pointer");
     *out = nullptr;
-    if (precision < TABNET_FP32 || precision > TABNET_BF16X3) return fail(TABNET_ERR_ARG, "unknown precision");
+    if (precision < TABNET_FP32 || precision > TABNET_BF16X6) return fail(TABNET_ERR_ARG, "unknown precision");
     tabnet_model* m = nullptr;
     try {
         m = new tabnet_model();
@@ -597,7 +597,7 @@ int tabnet_forward_segments(tabnet_model* m, const tabnet_segment* segs, int n_s
 
 int tabnet_set_tile_config(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm) {
     if (!m) return fail(TABNET_ERR_ARG, "null model");
-    if (m->precision != TABNET_BF16 && m->precision != TABNET_BF16X3)
+    if (m->precision == TABNET_FP32)
         return fail(TABNET_ERR_UNSUPPORTED_DIMS, "tile shapes apply to the tensor-core precisions");
     DeviceGuard guard(m->device);
     if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
@@ -615,7 +615,7 @@ int tabnet_set_tile_config(tabnet_model* m, int nwg, int n_slots, int ctas_per_s
 
 int tabnet_get_tile_config(const tabnet_model* m, int* nwg, int* n_slots, int* ctas_per_sm) {
     if (!m) return fail(TABNET_ERR_ARG, "null model");
-    if (m->precision != TABNET_BF16 && m->precision != TABNET_BF16X3)
+    if (m->precision == TABNET_FP32)
         return fail(TABNET_ERR_UNSUPPORTED_DIMS, "tile shapes apply to the tensor-core precisions");
     if (nwg) *nwg = m->tc_launch_cfg.nwg;
     if (n_slots) *n_slots = m->tc_launch_cfg.n_slots;

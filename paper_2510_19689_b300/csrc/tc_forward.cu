@@ -141,10 +141,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// Row r, K columns [16 ch, 16 ch + 16) of the A operand: bf16(v), and in
-// split mode also bf16(v - bf16(v)) into the low-half buffer.
-template <bool SPLIT>
-__device__ __forceinline__ void store_a16(uint8_t* sA, uint8_t* sAlo, int r, int ch, const float (&v)[16]) {
+// Row r, K columns [16 ch, 16 ch + 16) of the A operand as NP bf16 parts:
+// part 0 = bf16(v) into sA, and each further part the bf16 rounding of what
+// the earlier parts leave (v - hi, then v - hi - mid) into sAlo, one part
+// every `part_bytes`.  The remainders are exact in float32.
+template <int NP>
+__device__ __forceinline__ void store_a16(uint8_t* sA, uint8_t* sAlo, uint32_t part_bytes, int r, int ch,
+                                          const float (&v)[16]) {
     uint32_t w[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) w[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
@@ -152,28 +155,42 @@ __device__ __forceinline__ void store_a16(uint8_t* sA, uint8_t* sAlo, int r, int
     const uint32_t o1 = (uint32_t)((ch >> 2) * 16384) + sw128_off(r, (ch & 3) * 2 + 1);
     *reinterpret_cast<uint4*>(sA + o0) = make_uint4(w[0], w[1], w[2], w[3]);
     *reinterpret_cast<uint4*>(sA + o1) = make_uint4(w[4], w[5], w[6], w[7]);
-    if constexpr (SPLIT) {
+    if constexpr (NP >= 2) {
+        float rem[16];
         uint32_t l[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[j]);
-            const float2 hf = __bfloat1622float2(h);
-            l[j] = pack_bf16(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+            const float2 hf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[j]));
+            rem[2 * j] = v[2 * j] - hf.x;
+            rem[2 * j + 1] = v[2 * j + 1] - hf.y;
+            l[j] = pack_bf16(rem[2 * j], rem[2 * j + 1]);
         }
         *reinterpret_cast<uint4*>(sAlo + o0) = make_uint4(l[0], l[1], l[2], l[3]);
         *reinterpret_cast<uint4*>(sAlo + o1) = make_uint4(l[4], l[5], l[6], l[7]);
+        if constexpr (NP >= 3) {
+            uint32_t q[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float2 mf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&l[j]));
+                q[j] = pack_bf16(rem[2 * j] - mf.x, rem[2 * j + 1] - mf.y);
+            }
+            *reinterpret_cast<uint4*>(sAlo + part_bytes + o0) = make_uint4(q[0], q[1], q[2], q[3]);
+            *reinterpret_cast<uint4*>(sAlo + part_bytes + o1) = make_uint4(q[4], q[5], q[6], q[7]);
+        }
     }
 }
 
 // Row r, K columns [8 u, 8 u + 8) of the A operand (u = 8-column unit).
-template <bool SPLIT>
-__device__ __forceinline__ void store_a8(uint8_t* sA, uint8_t* sAlo, int r, int u, const float (&v)[8]) {
+template <int NP>
+__device__ __forceinline__ void store_a8(uint8_t* sA, uint8_t* sAlo, uint32_t part_bytes, int r, int u,
+                                         const float (&v)[8]) {
+    static_assert(NP <= 2, "the three-part split runs with one warpgroup (16-column pieces)");
     uint32_t w[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) w[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
     const uint32_t o = (uint32_t)((u >> 3) * 16384) + sw128_off(r, u & 7);
     *reinterpret_cast<uint4*>(sA + o) = make_uint4(w[0], w[1], w[2], w[3]);
-    if constexpr (SPLIT) {
+    if constexpr (NP >= 2) {
         uint32_t l[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -182,6 +199,7 @@ __device__ __forceinline__ void store_a8(uint8_t* sA, uint8_t* sAlo, int r, int 
         }
         *reinterpret_cast<uint4*>(sAlo + o) = make_uint4(l[0], l[1], l[2], l[3]);
     }
+    (void)part_bytes;
 }
 
 // Folded-BN vectors: staged in shared memory (epi_s != 0, a shared address)
@@ -195,7 +213,7 @@ __device__ __forceinline__ float4 ld_epi(const float* g, uint32_t epi_s, int idx
 // LEAN: the launch shape stages the BN shifts and the input cache in shared
 // memory and keeps the aggregate in TMEM, so the kernel is compiled with only
 // those paths (smaller code, fewer instruction misses).
-template <int N, int NWG, bool SPLIT, bool ZREG, bool LEAN>
+template <int N, int NWG, int NP, bool ZREG, bool LEAN>
 __global__ void __launch_bounds__(128 * NWG, (NWG == 2 && N <= 64) ? 2 : 1)
 tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* __restrict__ x_cat,
                   int64_t rows, float* __restrict__ logits, float* __restrict__ masks,
@@ -203,7 +221,8 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     constexpr int THREADS = 128 * NWG;
     constexpr int CPW = N / NWG;  // GLU output columns per warpgroup
     constexpr int RCH = CPW / 16;  // 16-column chunks per thread
-    constexpr int PARTS = SPLIT ? 2 : 1;  // weight chunks per 64-wide K block
+    constexpr bool SPLIT = NP >= 2;       // operands carried in several bf16 parts
+    constexpr int PARTS = NP;             // weight chunks (parts) per 64-wide K block
     constexpr int kZregChunks = zreg_chunks(NWG);
     static_assert(CPW % 16 == 0, "each warpgroup takes whole 16-column chunks");
 
@@ -215,6 +234,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 
     uint8_t* sA = smem + p.sm.a_hi;
     uint8_t* sAlo = SPLIT ? smem + p.sm.a_lo : nullptr;
+    const uint32_t a_part = SPLIT ? (uint32_t)(p.sm.a_lo - p.sm.a_hi) : 0u;  // bytes per operand part
     float* sAgg = reinterpret_cast<float*>(smem + (p.sm.agg >= 0 ? p.sm.agg : 0));
     float2* sX = reinterpret_cast<float2*>(smem + (p.sm.xch >= 0 ? p.sm.xch : 0));
     float* sWf = reinterpret_cast<float*>(smem + p.sm.wf);
@@ -235,7 +255,6 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     const uint32_t bar_empty = ptx::smem_u32(bars + S);
     const uint32_t bar_acc = ptx::smem_u32(bars + 2 * S);
     const uint32_t a_base = ptx::smem_u32(sA);
-    const uint32_t alo_base = SPLIT ? ptx::smem_u32(sAlo) : 0u;
     const uint32_t ring_base = ptx::smem_u32(smem + p.sm.ring);
 
     if (tid == 0) {
@@ -358,19 +377,47 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 if (!ok) break;
                 // descriptors of the block's first K step; a K step of 16
                 // bf16 (32 bytes) adds 2 to the encoded start address
-                const uint64_t d_bhi = ptx::sw128_desc(ring_base + (uint32_t)(slot_p[0] * p.slot_bytes));
-                const uint64_t d_blo = ptx::sw128_desc(ring_base + (uint32_t)(slot_p[PARTS - 1] * p.slot_bytes));
-                const uint64_t d_ahi = ptx::sw128_desc(a_base + (uint32_t)(b * 16384));
-                const uint64_t d_alo = ptx::sw128_desc(alo_base + (uint32_t)(b * 16384));
-                const int nk = min(4, kb - kk);
+                uint64_t d_b[PARTS], d_a[PARTS];  // part k of W and of A for this K block
 #pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) {
-                    if (k4 < nk) {
-                        const uint64_t step = 2u * (uint32_t)k4;
-                        ptx::mma_f16(tmem, d_ahi + step, d_bhi + step, idesc, (kk + k4) > 0 ? 1u : 0u);
-                        if constexpr (SPLIT) {
-                            ptx::mma_f16(tmem, d_ahi + step, d_blo + step, idesc, 1u);
-                            ptx::mma_f16(tmem, d_alo + step, d_bhi + step, idesc, 1u);
+                for (int part = 0; part < PARTS; ++part) {
+                    d_b[part] = ptx::sw128_desc(ring_base + (uint32_t)(slot_p[part] * p.slot_bytes));
+                    d_a[part] = ptx::sw128_desc(a_base + (uint32_t)part * a_part + (uint32_t)(b * 16384));
+                }
+                const int nk = min(4, kb - kk);
+                if constexpr (NP == 3) {
+                    // Products whose parts' significance reaches 2^-16 of hi hi:
+                    // the five small ones first, so that most additions into
+                    // the accumulator happen while it is still small (each
+                    // rounds relative to the running sum), then hi hi.
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        if (k4 < nk) {
+                            const uint64_t step = 2u * (uint32_t)k4;
+                            ptx::mma_f16(tmem, d_a[0] + step, d_b[1] + step, idesc, (kk + k4) > 0 ? 1u : 0u);
+                            ptx::mma_f16(tmem, d_a[1] + step, d_b[0] + step, idesc, 1u);
+                            ptx::mma_f16(tmem, d_a[0] + step, d_b[2] + step, idesc, 1u);
+                            ptx::mma_f16(tmem, d_a[1] + step, d_b[1] + step, idesc, 1u);
+                            ptx::mma_f16(tmem, d_a[2] + step, d_b[0] + step, idesc, 1u);
+                        }
+                    }
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        if (k4 < nk) {
+                            const uint64_t step = 2u * (uint32_t)k4;
+                            ptx::mma_f16(tmem, d_a[0] + step, d_b[0] + step, idesc, 1u);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        if (k4 < nk) {
+                            // hi hi; with two parts also hi lo and lo hi
+                            const uint64_t step = 2u * (uint32_t)k4;
+                            ptx::mma_f16(tmem, d_a[0] + step, d_b[0] + step, idesc, (kk + k4) > 0 ? 1u : 0u);
+                            if constexpr (NP >= 2) {
+                                ptx::mma_f16(tmem, d_a[0] + step, d_b[1] + step, idesc, 1u);
+                                ptx::mma_f16(tmem, d_a[1] + step, d_b[0] + step, idesc, 1u);
+                            }
                         }
                     }
                 }
@@ -614,7 +661,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 const int c = ch * 16 + j;
                 v[j] = has_f ? (c < de ? fc[c * kFStride + lt] : 0.f) : f_value(c, valid);
             }
-            store_a16<SPLIT>(sA, sAlo, lt, ch, v);
+            store_a16<NP>(sA, sAlo, a_part, lt, ch, v);
             uint32_t ones[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) ones[j] = 0x3f800000u;
@@ -831,7 +878,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                                 if (ch * 16 + j < de) mrow[ch * 16 + j] = mk[j];
                         }
                     }
-                    store_a16<SPLIT>(sA, sAlo, lt, ch, v);
+                    store_a16<NP>(sA, sAlo, a_part, lt, ch, v);
                 }
                 ptx::tmem_wait_st();
                 PH_MARK(3);
@@ -892,8 +939,8 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 if constexpr (NWG == 1) {
                     if (sc + 1 < NSUB) ptx::tmem_wait_ld(lin[cur ^ 1], gat[cur ^ 1]);
                 }
-                if constexpr (SW == 16) store_a16<SPLIT>(sA, sAlo, lt, c0 / 16, out);
-                else store_a8<SPLIT>(sA, sAlo, lt, c0 / 8, out);
+                if constexpr (SW == 16) store_a16<NP>(sA, sAlo, a_part, lt, c0 / 16, out);
+                else store_a8<NP>(sA, sAlo, a_part, lt, c0 / 8, out);
             }
             PH_MARK(4);
             if (++l < lpf) continue;
@@ -1094,8 +1141,13 @@ void pack_sw128(const float* W, int n_out, int k_valid, int col_shift, int k_pad
                 const int k = b * 64 + kk;
                 const int src = k - col_shift;
                 const float w = (src >= 0 && src < k_valid) ? W[(size_t)n * k_valid + src] : 0.f;
-                const uint16_t hi = f32_to_bf16_rne(w);
-                const uint16_t h = part == 0 ? hi : f32_to_bf16_rne(w - bf16_to_f32(hi));
+                // part 0: bf16(w); each further part: bf16 of what the earlier parts leave
+                float rem = w;
+                uint16_t h = f32_to_bf16_rne(rem);
+                for (int q = 1; q <= part; ++q) {
+                    rem -= bf16_to_f32(h);
+                    h = f32_to_bf16_rne(rem);
+                }
                 const size_t off = (size_t)(n >> 3) * 1024 + (n & 7) * 128 + ((((kk >> 3) ^ (n & 7)) & 7) << 4) +
                                    (kk & 7) * 2;
                 std::memcpy(blk + off, &h, 2);
@@ -1108,29 +1160,34 @@ int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
 struct Variant {
     int N, nwg;
-    bool split, zreg, lean;
+    int np;  // bf16 parts per operand: 1 (bf16), 2 (split-bf16), 3 (three-part split)
+    bool zreg, lean;
 };
 
 // Run f on the kernel instantiation of a variant; false when none exists.
 template <typename F>
 bool with_kernel(const Variant& v, F&& f) {
-#define TC_VAR4(NN, WW, SP, ZR)                                                      \
-    if (v.split == SP && v.zreg == ZR) {                                             \
-        if (v.lean) f(tc_forward_kernel<NN, WW, SP, ZR, true>);                       \
-        else f(tc_forward_kernel<NN, WW, SP, ZR, false>);                            \
+#define TC_VAR4(NN, WW, NP, ZR)                                                      \
+    if (v.np == NP && v.zreg == ZR) {                                                \
+        if (v.lean) f(tc_forward_kernel<NN, WW, NP, ZR, true>);                       \
+        else f(tc_forward_kernel<NN, WW, NP, ZR, false>);                            \
         return true;                                                                 \
     }
+// one warpgroup: 1, 2 or 3 parts, z in registers or TMEM
 #define TC_VARIANT(NN, WW)              \
     if (v.N == NN && v.nwg == WW) {     \
-        TC_VAR4(NN, WW, true, true)     \
-        TC_VAR4(NN, WW, true, false)    \
-        TC_VAR4(NN, WW, false, true)    \
-        TC_VAR4(NN, WW, false, false)   \
+        TC_VAR4(NN, WW, 3, true)        \
+        TC_VAR4(NN, WW, 3, false)       \
+        TC_VAR4(NN, WW, 2, true)        \
+        TC_VAR4(NN, WW, 2, false)       \
+        TC_VAR4(NN, WW, 1, true)        \
+        TC_VAR4(NN, WW, 1, false)       \
     }
+// two warpgroups: 1 or 2 parts, z in TMEM
 #define TC_VARIANT_NOZ(NN, WW)          \
     if (v.N == NN && v.nwg == WW) {     \
-        TC_VAR4(NN, WW, true, false)    \
-        TC_VAR4(NN, WW, false, false)   \
+        TC_VAR4(NN, WW, 2, false)       \
+        TC_VAR4(NN, WW, 1, false)       \
     }
     TC_VARIANT(16, 1)
     TC_VARIANT(32, 1)
@@ -1144,14 +1201,14 @@ bool with_kernel(const Variant& v, F&& f) {
     return false;
 }
 
-TcSmem smem_layout(int N, int dp, int de, int d, int n_cls, int n_d, int n_slots, int slot_bytes, bool split,
+TcSmem smem_layout(int N, int dp, int de, int d, int n_cls, int n_d, int n_slots, int slot_bytes, int np,
                    int nwg, int epi_floats, int n_chunks, bool agg_tmem, bool with_epi, bool with_f, bool with_mst) {
     TcSmem s{};
     const int a_blocks = (std::max(dp, N) + 63) / 64;
     int o = 0;
     s.a_hi = o; o += a_blocks * 16384;
-    s.a_lo = -1;
-    if (split) { s.a_lo = o; o += a_blocks * 16384; }
+    s.a_lo = -1;  // the further parts follow the first, a_blocks * 16 KB each
+    if (np > 1) { s.a_lo = o; o += (np - 1) * a_blocks * 16384; }
     s.ring = o; o += n_slots * slot_bytes;
     s.agg = -1;
     if (!agg_tmem) { s.agg = o; o += round_up(d * 128 * 4, 16); }
@@ -1177,17 +1234,32 @@ TcSmem smem_layout(int N, int dp, int de, int d, int n_cls, int n_d, int n_slots
 
 }  // namespace
 
+// bf16 parts per operand of a tensor-core precision (0: not offered).
+int precision_parts(int precision) {
+    switch (precision) {
+        case TABNET_BF16: return 1;
+        case TABNET_BF16X3: return 2;
+        case TABNET_BF16X6: return 3;
+    }
+    return 0;
+}
+
 int tc_build(tabnet_model* m, Arena& a, std::string* why) {
     const tabnet_dims& d = m->host.dims;
     const int N = d.n_d + d.n_a;
     const int dp = round_up(d.d_emb, 16);
-    const bool split = (m->precision == TABNET_BF16X3);
-    if (m->precision != TABNET_BF16 && m->precision != TABNET_BF16X3) {
+    const int np = precision_parts(m->precision);
+    const bool split = np > 1;
+    if (np == 0) {
         *why = "FP8 E4M3 is not offered: E4M3 operands move the sparsemax masks of most rows";
         return TABNET_ERR_UNSUPPORTED_DIMS;
     }
     if (N != 16 && N != 32 && N != 64 && N != 128) {
         *why = "tensor-core path needs n_d + n_a in {16, 32, 64, 128}";
+        return TABNET_ERR_UNSUPPORTED_DIMS;
+    }
+    if (np == 3 && N > 64) {
+        *why = "the three-part split (TABNET_BF16X6) needs n_d + n_a <= 64 (one warpgroup per row)";
         return TABNET_ERR_UNSUPPORTED_DIMS;
     }
     if (dp > 256) { *why = "tensor-core path needs d_emb <= 256"; return TABNET_ERR_UNSUPPORTED_DIMS; }
@@ -1214,8 +1286,8 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
     p.kn_blocks = (N + 63) / 64;
 
     const HostModel& hm = m->host;
-    const int parts = split ? 2 : 1;
-    // Every 64-wide K block of W (hi, then lo in split mode) becomes a chunk.
+    const int parts = np;
+    // Every 64-wide K block of W (its parts in order: hi, then lo or mid, lo) becomes a chunk.
     auto push_layer = [&](const float* W, int n_out, int k_valid, int col_shift, int k_pad,
                           std::vector<std::pair<size_t, uint32_t>>* keep) {
         const uint32_t cb = (uint32_t)n_out * 128;
@@ -1305,14 +1377,15 @@ int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std
     const tabnet_dims& d = m->host.dims;
     const int N = d.n_d + d.n_a;
     TcParams& p = m->tc;
-    const bool split = (m->precision == TABNET_BF16X3);
+    const int np = precision_parts(m->precision);
     if (nwg <= 0) nwg = (N == 128) ? 2 : 1;
     if (N == 128 && nwg != 2) { *why = "N = 128 needs two warpgroups"; return TABNET_ERR_UNSUPPORTED_DIMS; }
     if (N == 16 && nwg != 1) { *why = "N = 16 takes one warpgroup"; return TABNET_ERR_UNSUPPORTED_DIMS; }
     if (nwg != 1 && nwg != 2) { *why = "one or two warpgroups"; return TABNET_ERR_UNSUPPORTED_DIMS; }
+    if (np == 3 && nwg != 1) { *why = "the three-part split takes one warpgroup"; return TABNET_ERR_UNSUPPORTED_DIMS; }
     const int dch = p.dp / 16;
     const bool zreg = (dch + nwg - 1) / nwg <= zreg_chunks(nwg);
-    Variant v{N, nwg, split, zreg, false};
+    Variant v{N, nwg, np, zreg, false};
     cudaFuncAttributes fa{}, fa_lean{};
     if (!with_kernel(v, [&](auto fn) { cudaFuncGetAttributes(&fa, fn); })) {
         *why = "no kernel for this shape";
@@ -1330,7 +1403,7 @@ int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std
     const int reg_limit = 65536 / (((regs * 32 + 255) / 256 * 256) * (threads / 32));
     const int tmem_limit = 512 / p.tmem_cols;
     const int slot_bytes = std::max(2 * N, p.dp) * 128;
-    const int min_slots = split ? 2 : 1;
+    const int min_slots = np;  // one K block's parts
     int cps_max = std::max(1, std::min({tmem_limit, reg_limit, 4}));
     int best_cps = 0, best_slots = 0;
     bool best_epi = false, best_f = false, best_mst = false;
@@ -1346,7 +1419,7 @@ int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std
             int found = 0;
             for (int sl = 6; sl >= min_slots; --sl) {
                 if (n_slots > 0 && sl != n_slots) continue;
-                TcSmem sm = smem_layout(N, p.dp, d.d_emb, d.n_feat, d.n_classes, d.n_d, sl, slot_bytes, split, nwg,
+                TcSmem sm = smem_layout(N, p.dp, d.d_emb, d.n_feat, d.n_classes, d.n_d, sl, slot_bytes, np, nwg,
                                         p.epi_floats, p.chunks_per_tile, p.tm_agg >= 0, st[0], st[1], st[2]);
                 if ((size_t)sm.total <= budget) { found = sl; break; }
             }
@@ -1363,7 +1436,7 @@ int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std
     if (!best_cps) { *why = "no launch shape fits shared memory"; return TABNET_ERR_UNSUPPORTED_DIMS; }
     p.n_slots = best_slots;
     p.slot_bytes = slot_bytes;
-    p.sm = smem_layout(N, p.dp, d.d_emb, d.n_feat, d.n_classes, d.n_d, best_slots, slot_bytes, split, nwg,
+    p.sm = smem_layout(N, p.dp, d.d_emb, d.n_feat, d.n_classes, d.n_d, best_slots, slot_bytes, np, nwg,
                        p.epi_floats, p.chunks_per_tile, p.tm_agg >= 0, best_epi, best_f, best_mst);
     size_t smem = (size_t)p.sm.total + 1024;
     // request enough shared memory that no more than best_cps CTAs share an SM
@@ -1409,7 +1482,7 @@ cudaError_t tc_launch(tabnet_model* m, const float* x_num, const int* x_cat, int
     // a segmented launch learns its row count on the device: one CTA per slot
     const unsigned grid = (unsigned)(seg ? slots : std::min<int64_t>((rows + 127) / 128, slots));
     const dim3 block(128 * L.nwg);
-    const Variant v{p.m.N, L.nwg, m->precision == TABNET_BF16X3, L.zreg, L.lean};
+    const Variant v{p.m.N, L.nwg, precision_parts(m->precision), L.zreg, L.lean};
     const bool found = with_kernel(v, [&](auto fn) {
         fn<<<grid, block, L.smem, stream>>>(p, x_num, x_cat, rows, logits, masks, agg);
     });

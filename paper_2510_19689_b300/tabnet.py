@@ -17,8 +17,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtabnet.so")
 
-TABNET_FP32, TABNET_BF16, TABNET_FP8_E4M3, TABNET_BF16X3 = 0, 1, 2, 3
-PRECISIONS = {"fp32": TABNET_FP32, "bf16": TABNET_BF16, "fp8": TABNET_FP8_E4M3, "bf16x3": TABNET_BF16X3}
+TABNET_FP32, TABNET_BF16, TABNET_FP8_E4M3, TABNET_BF16X3, TABNET_BF16X6 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp32": TABNET_FP32, "bf16": TABNET_BF16, "fp8": TABNET_FP8_E4M3, "bf16x3": TABNET_BF16X3,
+              "bf16x6": TABNET_BF16X6}
 
 OK = 0
 ERR = {

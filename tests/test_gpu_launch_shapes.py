@@ -32,7 +32,7 @@ WIDTHS = {
                           gamma=1.3, n_classes=4),
 }
 ROWS = 3 * 128 + 45
-SHAPES = [(1, 2, 1), (1, 3, 1), (1, 2, 2), (1, 4, 2), (2, 2, 1), (2, 3, 1), (2, 2, 2)]
+SHAPES = [(1, 2, 1), (1, 3, 1), (1, 2, 2), (1, 3, 2), (1, 4, 2), (2, 2, 1), (2, 3, 1), (2, 2, 2)]
 
 
 @pytest.fixture(scope="module")
@@ -50,13 +50,15 @@ def _rows(spec, seed):
     return xn, xc
 
 
-@pytest.mark.parametrize("precision", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16", "bf16x6"])
 @pytest.mark.parametrize("width", sorted(WIDTHS))
 def test_every_launch_shape(tabnet_mod, width, precision):
     spec = WIDTHS[width]
+    if precision == "bf16x6" and width == 128:
+        pytest.skip("the three-part split takes n_d + n_a <= 64")
     params = synth.make_params(spec, 700 + width, bn_affine="random")
     xn, xc = _rows(spec, 800 + width)
-    ref = O.forward(params, xn, xc) if precision == "bf16x3" else None
+    ref = O.forward(params, xn, xc) if precision != "bf16" else None
     dev = torch.device("cuda", 0)
     m = tabnet_mod.Model(synth.to_blob(params), precision)
     xnd, xcd = torch.from_numpy(xn).to(dev), torch.from_numpy(xc).to(dev)
@@ -77,9 +79,14 @@ def test_every_launch_shape(tabnet_mod, width, precision):
         assert all(np.isfinite(g).all() for g in got), (nwg, slots, cps)
         if ref is not None:
             rl, rm, ra = ref
-            assert np.abs(got[0] - rl).max() <= 2e-2, (nwg, slots, cps)
-            assert np.abs(got[1] - rm).sum(axis=(1, 2)).max() <= 2e-2, (nwg, slots, cps)
-            assert np.abs(got[2] - ra).sum(axis=1).max() <= 2e-2, (nwg, slots, cps)
+            if precision == "bf16x3":
+                assert np.abs(got[0] - rl).max() <= 2e-2, (nwg, slots, cps)
+                assert np.abs(got[1] - rm).sum(axis=(1, 2)).max() <= 2e-2, (nwg, slots, cps)
+                assert np.abs(got[2] - ra).sum(axis=1).max() <= 2e-2, (nwg, slots, cps)
+            else:  # the float32 bar of the model-shape tests
+                assert (np.abs(got[0] - rl) / np.maximum(np.abs(rl), 1)).max() <= 5e-5, (nwg, slots, cps)
+                assert np.abs(got[1] - rm).sum(axis=(1, 2)).max() <= 5e-4, (nwg, slots, cps)
+                assert np.abs(got[2] - ra).sum(axis=1).max() <= 5e-4, (nwg, slots, cps)
         if nwg in seen:
             np.testing.assert_array_equal(seen[nwg][0], got[0])
             np.testing.assert_array_equal(seen[nwg][1], got[1])
@@ -88,4 +95,6 @@ def test_every_launch_shape(tabnet_mod, width, precision):
             seen[nwg] = got
         ran += 1
     m.close()
-    assert ran >= 2  # N = 128 runs two warpgroups at one CTA per SM only
+    # N = 128 runs two warpgroups at one CTA per SM only; the three-part split
+    # runs one warpgroup only
+    assert ran >= 2

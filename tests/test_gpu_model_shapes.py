@@ -38,7 +38,7 @@ SHAPES = {
 # stated bar, and float32 FMA chains through every layer on lognormal inputs
 # (|f| up to ~100, ~2^-24 relative per operation, a dozen layers) reach
 # ~2e-5 relative on the worst of a few hundred rows: gated at 5e-5.
-TOL = {"fp32": (5e-5, 5e-4), "bf16x3": (2e-2, 2e-2)}
+TOL = {"fp32": (5e-5, 5e-4), "bf16x3": (2e-2, 2e-2), "bf16x6": (5e-5, 5e-4)}
 
 
 @pytest.fixture(scope="module")
@@ -63,11 +63,18 @@ def _rows(spec, rows, seed):
     return xn, xc
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "bf16x6"])
 @pytest.mark.parametrize("name", sorted(SHAPES))
 def test_model_shape(tabnet_mod, name, precision):
     spec = _spec(name)
     params = synth.make_params(spec, 500 + sorted(SHAPES).index(name), bn_affine="random")
+    if precision == "bf16x6" and name == "wide_embedding":
+        # three 64-wide K blocks in three parts (144 KB of A operand) plus a
+        # three-slot ring leave no launch shape within shared memory
+        with pytest.raises(tabnet_mod.TabnetError) as e:
+            tabnet_mod.Model(synth.to_blob(params), precision)
+        assert e.value.code == -6 and "shared memory" in str(e.value)
+        return
     rows = 2 * 128 + 37
     xn, xc = _rows(spec, rows, 600)
     dev = torch.device("cuda", 0)
@@ -84,7 +91,7 @@ def test_model_shape(tabnet_mod, name, precision):
     rl, rm, ra = O.forward(params, xn, xc)
     lg, mk, ag = lg.cpu().numpy(), mk.cpu().numpy(), ag.cpu().numpy()
     logit_tol, mask_tol = TOL[precision]
-    if precision == "fp32":
+    if precision != "bf16x3":
         assert (np.abs(lg - rl) / np.maximum(np.abs(rl), 1)).max() <= logit_tol
     else:
         assert np.abs(lg - rl).max() <= logit_tol
