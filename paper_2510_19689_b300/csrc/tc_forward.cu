@@ -1,5 +1,6 @@
 // TabNet forward with the fully connected layers on the 5th-generation
-// tensor cores (tcgen05, sm_103a): the bf16 and split-bf16 precision modes.
+// tensor cores (tcgen05, sm_103a): the bf16, split-bf16 and three-part
+// (float32-accurate) precision modes.
 //
 // One CTA owns a tile of 128 rows for the whole forward pass: the embedding
 // and input BN, the step-0 feature transformer, then per decision step the
@@ -17,10 +18,12 @@
 //     activations (A) and the layer's weights (B) from shared memory in the
 //     128-byte-swizzled K-major layout and accumulating in fp32 in tensor
 //     memory (TMEM lane = row).  In split mode both operands are carried as
-//     hi + lo bf16 pairs and each K step issues hi*hi, hi*lo and lo*hi.  One
-//     phase loop walks a tile's layers, so there is one MMA issue site.
+//     hi + lo bf16 pairs and each K step issues hi*hi, hi*lo and lo*hi; with
+//     three parts (hi, lo, lo2) the five products down to 2^-16 of hi*hi go
+//     first and hi*hi last.  One phase loop walks a tile's layers, so there
+//     is one MMA issue site.
 //   * Weights stream from L2 through a ring of shared-memory slots filled by
-//     1-D bulk async copies (TMA engine), one 64-wide K block (hi or lo) per
+//     1-D bulk async copies (TMA engine), one part of a 64-wide K block per
 //     slot, pre-swizzled by the host.  Thread 0 issues copies and MMAs; each
 //     slot has a "full" barrier (copy landed); a slot read by a layer's last
 //     K block is free once the accumulator barrier fires, earlier blocks'
