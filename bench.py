@@ -453,7 +453,8 @@ def main():
         n_probe = {"c1": 256, "c2": 1024, "c3": 128}[name]
         rp, cores, _ = oracle_rows_per_s(params, x_num_h[:n_probe], x_cat_h[:n_probe])
         n_cpu = int(min(rows, max(n_probe, rp * 10.0)))
-        reps = max(1, int(round(rp * 10.0 / n_cpu)))
+        _, _, t_one = oracle_rows_per_s(params, x_num_h[:n_cpu], x_cat_h[:n_cpu])  # one pass at full size
+        reps = max(1, int(round(10.0 / t_one)))
         t0 = time.perf_counter()
         for _ in range(reps):
             O.forward(params, x_num_h[:n_cpu], x_cat_h[:n_cpu])
@@ -467,7 +468,8 @@ def main():
         code = ("import sys, time, json; sys.path.insert(0, %r); from paper_2510_19689_b300 import synth; "
                 "from oracle import tabnet_oracle as O; p, _, xn, xc = synth.load_config(%r); "
                 "t = time.perf_counter(); O.forward(p, xn[:%d], xc[:%d]); r = %d / (time.perf_counter() - t); "
-                "n = int(min(len(xn), max(%d, r * 5.0))); k = max(1, int(round(r * 5.0 / n))); "
+                "n = int(min(len(xn), max(%d, r * 5.0))); "
+                "t = time.perf_counter(); O.forward(p, xn[:n], xc[:n]); k = max(1, int(round(5.0 / (time.perf_counter() - t)))); "
                 "t = time.perf_counter(); [O.forward(p, xn[:n], xc[:n]) for _ in range(k)]; "
                 "dt = time.perf_counter() - t; print(json.dumps([n * k / dt, n, k, dt]))"
                 ) % (ROOT, name, n_probe, n_probe, n_probe, n_probe)
