@@ -44,6 +44,9 @@ __device__ __forceinline__ int sum4i(int v) {
 __device__ __forceinline__ float sigmoid_exact(float x) { return 1.0f / (1.0f + expf(-x)); }
 
 // One GLU layer for the calling row: nxt[c] = GLU(BN(W cur))[c] (+ residual).
+// The gate product and the residual are rounded separately (__fmul_rn,
+// __fadd_rn): whether the compiler would contract them into an FMA depends
+// on the surrounding code, and the two forms differ in the last bits.
 template <int ROWS>
 __device__ __forceinline__ void glu_layer(const SimtLayer& L, const float* cur, float* nxt,
                                           bool first, int N, int r, int q) {
@@ -72,24 +75,99 @@ __device__ __forceinline__ void glu_layer(const SimtLayer& L, const float* cur, 
             if (c < N) {
                 const float ul = fmaf(lin[b], __ldg(L.scale + c), __ldg(L.shift + c));
                 const float ug = fmaf(gate[b], __ldg(L.scale + N + c), __ldg(L.shift + N + c));
-                const float g = ul * sigmoid_exact(ug);
-                nxt[c * ROWS + r] = first ? g : (cur[c * ROWS + r] + g) * kSqrtHalf;
+                const float g = __fmul_rn(ul, sigmoid_exact(ug));
+                nxt[c * ROWS + r] = first ? g : __fmul_rn(__fadd_rn(cur[c * ROWS + r], g), kSqrtHalf);
             }
         }
     }
 }
 
+template <int CT>
+__device__ __forceinline__ void load_w(const float* __restrict__ w, float (&o)[CT]) {
+    if constexpr (CT % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < CT; j += 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(w + j));
+            o[j] = v.x; o[j + 1] = v.y; o[j + 2] = v.z; o[j + 3] = v.w;
+        }
+    } else if constexpr (CT == 2) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(w));
+        o[0] = v.x; o[1] = v.y;
+    } else {
+#pragma unroll
+        for (int j = 0; j < CT; ++j) o[j] = __ldg(w + j);
+    }
+}
+
+// The same layer for all ROWS rows of the CTA at once, N = 16 CT: thread t
+// takes rows 4 (t mod ROWS/4) + [0, 4) and outputs CT (t div ROWS/4) + [0, CT)
+// (with their gates), so each weight it loads serves four rows and each
+// input value CT outputs.  Every output is the same sequential FMA chain over
+// k as in glu_layer, so the results are identical.  The caller synchronises
+// the CTA before (cur complete) and after (nxt complete).
+template <int ROWS, int CT>
+__device__ __forceinline__ void glu_layer_tiled(const SimtLayer& L, const float* cur, float* nxt, bool first,
+                                                int N) {
+    constexpr int RG = ROWS / 4;
+    const int rg = (int)threadIdx.x % RG, c0 = ((int)threadIdx.x / RG) * CT;
+    const float* __restrict__ wt = L.wt;
+    const int two_n = 2 * N;
+    float lin[4][CT], gate[4][CT];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < CT; ++j) { lin[i][j] = 0.f; gate[i][j] = 0.f; }
+    for (int k = 0; k < L.k; ++k) {
+        const float4 xv = *reinterpret_cast<const float4*>(cur + k * ROWS + 4 * rg);
+        const float x[4] = {xv.x, xv.y, xv.z, xv.w};
+        float wl[CT], wg[CT];
+        load_w<CT>(wt + (size_t)k * two_n + c0, wl);
+        load_w<CT>(wt + (size_t)k * two_n + N + c0, wg);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < CT; ++j) {
+                lin[i][j] = fmaf(wl[j], x[i], lin[i][j]);
+                gate[i][j] = fmaf(wg[j], x[i], gate[i][j]);
+            }
+    }
+#pragma unroll
+    for (int j = 0; j < CT; ++j) {
+        const int c = c0 + j;
+        const float sl = __ldg(L.scale + c), tl = __ldg(L.shift + c);
+        const float sg = __ldg(L.scale + N + c), tg = __ldg(L.shift + N + c);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = 4 * rg + i;
+            const float ul = fmaf(lin[i][j], sl, tl);
+            const float ug = fmaf(gate[i][j], sg, tg);
+            // separately rounded, as in glu_layer (no contraction into an FMA)
+            const float g = __fmul_rn(ul, sigmoid_exact(ug));
+            nxt[c * ROWS + r] = first ? g : __fmul_rn(__fadd_rn(cur[c * ROWS + r], g), kSqrtHalf);
+        }
+    }
+}
+
 // Feature transformer s on `in` (k = de for the first layer).  Returns the
-// buffer holding its N outputs.
+// buffer holding its N outputs.  Widths 16, 32, 64 and 128 run the
+// CTA-wide tiled layer, others the per-row one.
 template <int ROWS>
 __device__ __forceinline__ float* feature_transformer(const SimtParams& p, int s, const float* in,
                                                       float* b0, float* b1, int r, int q) {
-    const int lpf = p.m.layers_per_ft;
+    const int lpf = p.m.layers_per_ft, N = p.m.N;
     const float* cur = in;
     float* nxt = b1;
+    __syncthreads();  // every row's input is in place
     for (int l = 0; l < lpf; ++l) {
-        glu_layer<ROWS>(p.ft[s * lpf + l], cur, nxt, l == 0, p.m.N, r, q);
-        __syncwarp(row_mask());
+        const SimtLayer& L = p.ft[s * lpf + l];
+        switch (N) {
+            case 16: glu_layer_tiled<ROWS, 1>(L, cur, nxt, l == 0, N); break;
+            case 32: glu_layer_tiled<ROWS, 2>(L, cur, nxt, l == 0, N); break;
+            case 64: glu_layer_tiled<ROWS, 4>(L, cur, nxt, l == 0, N); break;
+            case 128: glu_layer_tiled<ROWS, 8>(L, cur, nxt, l == 0, N); break;
+            default: glu_layer<ROWS>(L, cur, nxt, l == 0, N, r, q);
+        }
+        __syncthreads();
         cur = nxt;
         nxt = (nxt == b1) ? b0 : b1;
     }

@@ -273,3 +273,21 @@ def test_outputs_past_the_int32_element_range(tabnet_mod):
     sample = (lg[it].cpu().numpy(), mk[it].cpu().numpy(), ag[it].cpu().numpy())
     del lg, mk, ag
     check("bf16x3", sample, O.forward(params, x_num[idx], x_cat[idx]))
+
+
+def test_fp32_width_outside_the_tiled_layer(tabnet_mod):
+    """n_d + n_a = 24: the float32 path runs its per-row GLU layer (the
+    CTA-wide tiled layer takes widths 16, 32, 64 and 128) and the tensor-core
+    modes refuse the width; the float32 results meet the float32 bar."""
+    spec = synth.TabNetSpec(n_num=7, cat_card=(5, 9), cat_emb_dim=(1, 2), n_d=12, n_a=12, n_steps=3, gamma=1.3,
+                            n_classes=3)
+    params = synth.make_params(spec, 90, bn_affine="random")
+    rng = np.random.default_rng(91)
+    x_num = rng.lognormal(0.0, 1.0, size=(333, spec.n_num)).astype(np.float32)
+    x_cat = np.stack([rng.integers(0, c, size=333) for c in spec.cat_card], axis=1).astype(np.int32)
+    blob = synth.to_blob(params)
+    gpu, status = run_gpu(tabnet_mod, blob, "fp32", x_num, x_cat)
+    assert status == 0
+    check("fp32", gpu, O.forward(params, x_num, x_cat))
+    with pytest.raises(tabnet_mod.TabnetError):
+        tabnet_mod.Model(blob, "bf16x3")
