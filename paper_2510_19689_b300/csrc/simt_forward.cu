@@ -117,6 +117,7 @@ __device__ __forceinline__ void glu_layer_tiled(const SimtLayer& L, const float*
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < CT; ++j) { lin[i][j] = 0.f; gate[i][j] = 0.f; }
+#pragma unroll 4
     for (int k = 0; k < L.k; ++k) {
         const float4 xv = *reinterpret_cast<const float4*>(cur + k * ROWS + 4 * rg);
         const float x[4] = {xv.x, xv.y, xv.z, xv.w};
