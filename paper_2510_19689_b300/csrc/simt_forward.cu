@@ -149,6 +149,55 @@ __device__ __forceinline__ void glu_layer_tiled(const SimtLayer& L, const float*
     }
 }
 
+// The attentive layer for all ROWS rows of the CTA at once, as the tiled GLU
+// layer: thread t takes rows 4 (t mod ROWS/4) + [0, 4) and the columns
+// c = t div ROWS/4 + 16 j (j < ceil(de / 16) <= kAttMaxCt).  Each output is
+// the same sequential FMA chain over k as the per-row form.  The caller
+// synchronises the CTA afterwards (z complete); a (the transformer output's
+// attention part) and P are complete before (the feature transformer ends
+// with a CTA barrier).
+constexpr int kAttMaxCt = 16;
+
+template <int ROWS>
+__device__ __forceinline__ void attentive_tiled(const SimtLayer& A, const float* a, const float* P, float* Z,
+                                                int de, int n_a) {
+    constexpr int RG = ROWS / 4;
+    const int rg = (int)threadIdx.x % RG, cg = (int)threadIdx.x / RG;
+    const int ct = (de + 15) / 16;
+    float acc[4][kAttMaxCt];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < kAttMaxCt; ++j) acc[i][j] = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < n_a; ++k) {
+        const float4 xv = *reinterpret_cast<const float4*>(a + k * ROWS + 4 * rg);
+        const float x[4] = {xv.x, xv.y, xv.z, xv.w};
+        const float* w = A.wt + (size_t)k * de;
+#pragma unroll
+        for (int j = 0; j < kAttMaxCt; ++j) {
+            const int c = cg + 16 * j;
+            if (j < ct && c < de) {
+                const float wv = __ldg(w + c);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i][j] = fmaf(wv, x[i], acc[i][j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kAttMaxCt; ++j) {
+        const int c = cg + 16 * j;
+        if (j < ct && c < de) {
+            const float sc = __ldg(A.scale + c), sh = __ldg(A.shift + c);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = 4 * rg + i;
+                Z[c * ROWS + r] = fmaf(acc[i][j], sc, sh) * P[c * ROWS + r];
+            }
+        }
+    }
+}
+
 // Feature transformer s on `in` (k = de for the first layer).  Returns the
 // buffer holding its N outputs.  Widths 16, 32, 64 and 128 run the
 // CTA-wide tiled layer, others the per-row one.
@@ -227,14 +276,19 @@ simt_forward_kernel(const SimtParams p, const float* __restrict__ x_num,
     for (int i = 0; i < m.n_steps; ++i) {
         // Attentive transformer: z = BN(W_att a) * P.
         const SimtLayer& A = p.att[i];
-        for (int c = q; c < de; c += TPR) {
-            float acc = 0.f;
-            for (int k = 0; k < m.n_a; ++k)
-                acc = fmaf(__ldg(A.wt + (size_t)k * de + c), out[(n_d + k) * ROWS + r], acc);
-            const float u = fmaf(acc, __ldg(A.scale + c), __ldg(A.shift + c));
-            Z[c * ROWS + r] = u * P[c * ROWS + r];
+        if (de <= 16 * kAttMaxCt) {
+            attentive_tiled<ROWS>(A, out + n_d * ROWS, P, Z, de, m.n_a);
+            __syncthreads();  // every row's z is in place
+        } else {
+            for (int c = q; c < de; c += TPR) {
+                float acc = 0.f;
+                for (int k = 0; k < m.n_a; ++k)
+                    acc = fmaf(__ldg(A.wt + (size_t)k * de + c), out[(n_d + k) * ROWS + r], acc);
+                const float u = fmaf(acc, __ldg(A.scale + c), __ldg(A.shift + c));
+                Z[c * ROWS + r] = u * P[c * ROWS + r];
+            }
+            __syncwarp(row_mask());
         }
-        __syncwarp(row_mask());
         // Sparsemax by Michelot's fixed point: tau = (sum_S z - 1) / |S| over
         // S = {z > tau}, starting from S = all columns, until S stops shrinking.
         float s = 0.f;
