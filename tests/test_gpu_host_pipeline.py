@@ -41,7 +41,7 @@ def _device_forward(m, x_num, x_cat, masks, agg):
 # the aggregate (848 output bytes per row), 6 with masks only, 2 with the
 # aggregate only, and one with logits alone.
 @pytest.mark.parametrize("masks,agg", [(True, True), (True, False), (False, True), (False, False)])
-@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16x6", "fp32"])
 def test_chunked_host_forward_equals_one_launch(tabnet_mod, precision, masks, agg):
     params = synth.make_params(synth.SPECS["c2"], 31, bn_affine="random")
     x_num, x_cat = synth.make_rows("c2", 70001, seed=32)

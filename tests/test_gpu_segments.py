@@ -45,7 +45,7 @@ def _requests(name, sizes, seed):
     return reqs
 
 
-@pytest.mark.parametrize("precision", ["bf16x3", "bf16", "fp32"])
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16", "bf16x6", "fp32"])
 def test_segments_equal_single_forwards(tn, precision):
     params = synth.make_params(synth.SPECS["c2"], 31, bn_affine="random")
     m = tn.Model(synth.to_blob(params), precision)
