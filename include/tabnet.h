@@ -79,8 +79,11 @@ typedef enum {
                              values), six bf16 MMAs per K step (every product
                              down to 2^-16 of hi*hi) into one fp32 accumulator;
                              meets the float32 tolerances.  Needs
-                             n_d + n_a <= 64 (TABNET_ERR_UNSUPPORTED_DIMS
-                             otherwise) */
+                             n_d + n_a <= 64 and a launch shape within shared
+                             memory (three A-operand parts and three ring
+                             slots: wide embeddings with multi-column
+                             features may not fit); tabnet_create returns
+                             TABNET_ERR_UNSUPPORTED_DIMS otherwise */
 } tabnet_precision;
 
 /* Model shape, as read from a blob. */
