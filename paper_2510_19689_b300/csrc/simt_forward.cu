@@ -360,13 +360,6 @@ size_t simt_smem_bytes(const ModelConsts& m, int rows_per_cta) {
     return (size_t)(3 * m.de + kmax + m.N + m.d + m.n_d) * rows_per_cta * sizeof(float);
 }
 
-// Largest rows-per-CTA in {32, 16, 8} whose shared memory fits, 0 if none.
-int simt_pick_rows(const ModelConsts& m, size_t smem_limit) {
-    for (int r : {32, 16, 8})
-        if (simt_smem_bytes(m, r) <= smem_limit) return r;
-    return 0;
-}
-
 int simt_occupancy(int rows_per_cta, size_t smem) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;

@@ -20,7 +20,6 @@ namespace tabnet {
 
 // simt_forward.cu
 size_t simt_smem_bytes(const ModelConsts& m, int rows_per_cta);
-int simt_pick_rows(const ModelConsts& m, size_t smem_limit);
 cudaError_t simt_configure(int rows_per_cta, size_t smem);
 cudaError_t simt_launch(const SimtParams& p, int rows_per_cta, const float* x_num, const int* x_cat,
                         int64_t rows, float* logits, float* masks, float* agg, cudaStream_t stream,
@@ -327,14 +326,27 @@ int tabnet_create(const void* blob, size_t blob_bytes, int precision, int device
         if (precision == TABNET_FP32) {
             m->simt.m = m->consts;
             patch_simt(simt_lay, arena, base, m->simt);
-            m->simt_rows = simt_pick_rows(m->consts, m->smem_optin);
+            // rows per CTA: the most rows resident per SM (CTAs per SM x rows
+            // per CTA, registers and shared memory permitting), more rows per
+            // CTA on a tie
+            m->simt_rows = 0;
+            int best_resident = 0;
+            for (int r : {32, 16, 8}) {
+                const size_t sm = simt_smem_bytes(m->consts, r);
+                if (sm > m->smem_optin) continue;
+                if ((e = simt_configure(r, sm)) != cudaSuccess) {
+                    tabnet_destroy(m);
+                    return cuda_fail(e, "cudaFuncSetAttribute");
+                }
+                const int resident = simt_occupancy(r, sm) * r;
+                if (resident > best_resident) {
+                    best_resident = resident;
+                    m->simt_rows = r;
+                }
+            }
             if (m->simt_rows == 0) {
                 tabnet_destroy(m);
                 return fail(TABNET_ERR_UNSUPPORTED_DIMS, "model state does not fit in shared memory");
-            }
-            if ((e = simt_configure(m->simt_rows, simt_smem_bytes(m->consts, m->simt_rows))) != cudaSuccess) {
-                tabnet_destroy(m);
-                return cuda_fail(e, "cudaFuncSetAttribute");
             }
             m->simt_max_ctas = m->num_sms * simt_occupancy(m->simt_rows, simt_smem_bytes(m->consts, m->simt_rows));
         } else {
