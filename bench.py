@@ -521,7 +521,17 @@ def main():
                 m2.forward(s["xn"], s["xc"], rows, s["lg"], s["mk"], s["ag"], stream=stream)
             b1.record(stream)
             b1.synchronize()
-            extras[f"fused_{prec}"] = {"value": rows / (b0.elapsed_time(b1) / reps / 1e3), "unit": UNIT}
+            # the same 256 sampled rows against the FP64 oracle
+            m2.forward(s0["xn"], s0["xc"], rows, s0["lg"], s0["mk"], s0["ag"], stream=stream)
+            torch.cuda.synchronize()
+            lg2 = s0["lg"][it].cpu().numpy()
+            mk2 = s0["mk"][it].cpu().numpy()
+            ag2 = s0["ag"][it].cpu().numpy()
+            extras[f"fused_{prec}"] = {
+                "value": rows / (b0.elapsed_time(b1) / reps / 1e3), "unit": UNIT,
+                "parity": {"logit_rel_max": float((np.abs(lg2 - rl) / np.maximum(np.abs(rl), 1)).max()),
+                           "mask_l1_max": float(np.abs(mk2 - rm).sum((1, 2)).max()),
+                           "agg_l1_max": float(np.abs(ag2 - ra).sum(1).max()), "status": m2.poll_status()}}
             m2.close()
 
     if rank == 0 and not args.no_extras and args.precision != "fp32":
