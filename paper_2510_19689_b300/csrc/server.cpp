@@ -69,6 +69,7 @@ struct Batch {
     size_t in_num = 0, in_cat = 0, out_lg = 0, out_mk = 0, out_ag = 0;  // offsets inside the region
     std::vector<uint64_t> tickets;
     cudaEvent_t done = nullptr;
+    Clock::time_point t_launch;
     bool complete = false;
     int released = 0;
 };
@@ -85,6 +86,7 @@ struct ModelCtx {
     std::vector<cudaStream_t> streams;
     int next_stream = 0;
     int running = 0;               // batches launched and not yet complete
+    int64_t pending_rows = 0;      // rows of the pending requests
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -156,10 +158,17 @@ void engine_loop(tabnet_server* S) {
         // another stream)
         for (auto& mc : S->models) {
             uint64_t blocked = 0;  // bit i: stream i has a batch still running
+            const auto t_now = Clock::now();
             for (Batch* b : mc.inflight) {
                 if (b->complete) continue;
                 const uint64_t bit = 1ull << (b->stream_idx & 63);
                 if (blocked & bit) continue;
+                // no batch completes within 20 us of its launch (copies and
+                // one kernel): do not spend a query on it
+                if (t_now - b->t_launch < std::chrono::microseconds(20)) {
+                    blocked |= bit;
+                    continue;
+                }
                 const cudaError_t q = cudaEventQuery(b->done);
                 if (q == cudaErrorNotReady) {
                     blocked |= bit;
@@ -202,6 +211,12 @@ void engine_loop(tabnet_server* S) {
                 std::lock_guard<std::mutex> lk(S->mu);
                 // only batches still on the GPU count; finished results hold ring memory instead
                 if (mc.pending.empty() || mc.running >= S->cfg.max_inflight_batches) continue;
+                // Under load (half the model's streams busy) a small batch waits
+                // for more requests -- up to 200 us for its oldest -- so that the
+                // engine's fixed cost per launch is shared by more rows.
+                if (mc.running >= std::max(2, S->cfg.streams_per_model / 2) && mc.pending_rows < 512 &&
+                    Clock::now() - mc.pending.front()->t_submit < std::chrono::microseconds(200))
+                    continue;
                 while (!mc.pending.empty()) {
                     Request* r = mc.pending.front();
                     const int64_t nr = rows + r->rows;
@@ -210,6 +225,7 @@ void engine_loop(tabnet_server* S) {
                     if (need > mc.cap) {
                         if (take.empty()) {  // could never fit: reject
                             mc.pending.pop_front();
+                            mc.pending_rows -= r->rows;
                             S->reqs.erase(r->ticket);
                             ++S->rejected;
                             delete r;
@@ -220,11 +236,15 @@ void engine_loop(tabnet_server* S) {
                     take.push_back(r);
                     rows = nr;
                     mc.pending.pop_front();
+                    mc.pending_rows -= r->rows;
                 }
                 if (take.empty()) continue;
                 bytes = 5 * 256 + (size_t)rows * (mc.in_row + mc.out_row);
                 if (!ring_alloc(mc, bytes, &off)) {  // no room now: admission waits for memory
-                    for (auto it = take.rbegin(); it != take.rend(); ++it) mc.pending.push_front(*it);
+                    for (auto it = take.rbegin(); it != take.rend(); ++it) {
+                        mc.pending.push_front(*it);
+                        mc.pending_rows += (*it)->rows;
+                    }
                     continue;
                 }
             }
@@ -266,6 +286,7 @@ void engine_loop(tabnet_server* S) {
                                     (float*)(dv + b->out_lg), (float*)(dv + b->out_mk), (float*)(dv + b->out_ag), st);
             cudaMemcpyAsync(h + b->out_lg, dv + b->out_lg, b->bytes - b->out_lg - 0, cudaMemcpyDeviceToHost, st);
             cudaEventRecord(b->done, st);
+            b->t_launch = Clock::now();
             {
                 std::lock_guard<std::mutex> lk(S->mu);
                 if (rc != TABNET_OK && S->error == TABNET_OK) S->error = rc;
@@ -352,6 +373,7 @@ int tabnet_server_submit(tabnet_server* S, int model, const float* x_num, const 
         std::lock_guard<std::mutex> lk(S->mu);
         S->reqs.emplace(r->ticket, r);
         S->models[model].pending.push_back(r);
+        S->models[model].pending_rows += rows;
         ++S->submitted;
     }
     S->cv.notify_all();

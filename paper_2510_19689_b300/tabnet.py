@@ -360,8 +360,9 @@ class Server:
     def reset_stats(self) -> None:
         _check(lib().tabnet_server_reset_stats(self._h), "tabnet_server_reset_stats")
 
-    def replay(self, requests, release: bool = True) -> None:
-        """requests: list of (model, x_num, x_cat, arrival_s) with numpy inputs."""
+    def prepare_replay(self, requests):
+        """The C request array for replay_prepared (marshalling only):
+        requests is a list of (model, x_num, x_cat, arrival_s), numpy inputs."""
         arr = (ServerRequest * len(requests))()
         keep = []
         for i, (model, xn, xc, t) in enumerate(requests):
@@ -371,7 +372,15 @@ class Server:
             d = self.models[model].dims
             rows = xn.shape[0] if d.n_num else xc.shape[0]
             arr[i] = ServerRequest(model, _ptr(xn) if d.n_num else None, _ptr(xc) if d.n_cat else None, rows, t)
-        _check(lib().tabnet_server_replay(self._h, arr, len(requests), 1 if release else 0), "tabnet_server_replay")
+        return arr, keep
+
+    def replay_prepared(self, prepared, release: bool = True) -> None:
+        arr, _ = prepared
+        _check(lib().tabnet_server_replay(self._h, arr, len(arr), 1 if release else 0), "tabnet_server_replay")
+
+    def replay(self, requests, release: bool = True) -> None:
+        """requests: list of (model, x_num, x_cat, arrival_s) with numpy inputs."""
+        self.replay_prepared(self.prepare_replay(requests), release)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
