@@ -510,7 +510,11 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         for (int j = 0; j < 16; ++j) mstw[lane * 17 + j] = v[j];
         __syncwarp();
         const int c = lane & 15;
-#pragma unroll 4
+        // fully unrolled the row pointers and values of all 16 pieces load
+        // together (+3 % at 35 inputs); by 4 with two warpgroups, whose
+        // 128-register budget it would otherwise spill
+        constexpr int kStageUnroll = NWG == 1 ? 16 : 4;
+#pragma unroll kStageUnroll
         for (int i = 0; i < 16; ++i) {
             const int r = 2 * i + (lane >> 4);
             float* dst = rowptr[(warp & 3) * 32 + r];
