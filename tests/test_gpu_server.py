@@ -126,3 +126,48 @@ def test_poisson_replay(models):
     assert st["rows_completed"] == int(sizes.sum())
     assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
     srv.close()
+
+
+def test_same_result_under_the_default_policy(models):
+    """Default server shape (8 streams and 32 in-flight batches per model,
+    adaptive batching under load) with a float32-accurate model resident
+    beside the split-bf16 ones: requests answered inside a dense burst equal
+    the same requests answered alone, bit for bit."""
+    tabnet, params, ms = models
+    p6 = synth.make_params(synth.SPECS["c2"], 79, bn_affine="random")
+    m6 = tabnet.Model(synth.to_blob(p6), "bf16x6")
+    resident = ms + [m6]
+    names = NAMES + ["c2"]
+    srv = tabnet.Server(resident, device_bytes=512 << 20)
+    targets = [(i, *_req(names[i], r, 200 + i)) for i, r in zip(range(4), [5, 77, 33, 260])]
+    alone = []
+    for i, xn, xc in targets:
+        t = srv.submit(i, xn, xc)
+        srv.wait(t)
+        alone.append(srv.result(t))
+        srv.release(t)
+    rng = np.random.default_rng(6)
+    tickets, mine = [], {}
+    for k in range(2000):
+        i = int(rng.integers(4))
+        tickets.append(srv.submit(i, *_req(names[i], int(rng.integers(1, 120)), 3000 + k)))
+        if k % 500 == 250:
+            j = k // 500
+            mine[j] = srv.submit(targets[j][0], targets[j][1], targets[j][2])
+    for j, t in mine.items():
+        srv.wait(t)
+        for a, b in zip(alone[j], srv.result(t)):
+            np.testing.assert_array_equal(a, b)
+        srv.release(t)
+    for t in tickets:
+        srv.wait(t)
+        srv.release(t)
+    st = srv.stats()
+    assert st["rejected"] == 0 and st["completed"] == st["submitted"]
+    srv.close()
+    m6.close()
+    # the float32-accurate model's answer against the oracle at the float32 bar
+    i, xn, xc = targets[3]
+    lg = alone[3][0]
+    rl = O.forward(p6, xn, xc)[0]
+    assert (np.abs(lg - rl) / np.maximum(np.abs(rl), 1)).max() <= 1e-5
