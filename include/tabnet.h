@@ -267,12 +267,13 @@ typedef struct {
     size_t device_bytes;       /* device memory for all rings (0: 1 GiB), split by bytes per row */
     int max_batch_rows;        /* rows per batch at most (0: 65536) */
     int max_inflight_batches;  /* batches per model running on the GPU at once (0: 32); finished
-                                  but unreleased results hold ring memory, not a slot.  Once
-                                  half of the model's streams are busy, a batch of fewer than
-                                  512 rows waits for more requests, up to 200 us for its
-                                  oldest, so that one launch serves more rows under load */
+                                  but unreleased results hold ring memory, not a slot */
     int streams_per_model;     /* CUDA streams per model (0: 8, at most 64): small batches of
                                   one model run side by side on different SMs */
+    int batch_min_rows;        /* adaptive batching: once half of a model's streams are busy, a
+                                  batch of fewer rows than this (0: 512; < 0: off) waits ... */
+    int batch_wait_us;         /* ... for more requests, at most this long for its oldest
+                                  (0: 200 us), so that one launch serves more rows under load */
 } tabnet_server_config;
 
 typedef struct {

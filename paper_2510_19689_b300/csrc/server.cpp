@@ -212,10 +212,11 @@ void engine_loop(tabnet_server* S) {
                 // only batches still on the GPU count; finished results hold ring memory instead
                 if (mc.pending.empty() || mc.running >= S->cfg.max_inflight_batches) continue;
                 // Under load (half the model's streams busy) a small batch waits
-                // for more requests -- up to 200 us for its oldest -- so that the
-                // engine's fixed cost per launch is shared by more rows.
-                if (mc.running >= std::max(2, S->cfg.streams_per_model / 2) && mc.pending_rows < 512 &&
-                    Clock::now() - mc.pending.front()->t_submit < std::chrono::microseconds(200))
+                // for more requests -- up to batch_wait_us for its oldest -- so
+                // that the engine's fixed cost per launch is shared by more rows.
+                if (S->cfg.batch_min_rows > 0 && mc.running >= std::max(2, S->cfg.streams_per_model / 2) &&
+                    mc.pending_rows < S->cfg.batch_min_rows &&
+                    Clock::now() - mc.pending.front()->t_submit < std::chrono::microseconds(S->cfg.batch_wait_us))
                     continue;
                 while (!mc.pending.empty()) {
                     Request* r = mc.pending.front();
@@ -318,6 +319,8 @@ int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet
     S->cfg.max_batch_rows = cfg && cfg->max_batch_rows > 0 ? cfg->max_batch_rows : 65536;
     S->cfg.max_inflight_batches = cfg && cfg->max_inflight_batches > 0 ? cfg->max_inflight_batches : 32;
     S->cfg.streams_per_model = cfg && cfg->streams_per_model > 0 ? std::min(cfg->streams_per_model, 64) : 8;
+    S->cfg.batch_min_rows = cfg && cfg->batch_min_rows != 0 ? cfg->batch_min_rows : 512;
+    S->cfg.batch_wait_us = cfg && cfg->batch_wait_us > 0 ? cfg->batch_wait_us : 200;
     S->device = models[0]->device;
     int prev = 0;
     cudaGetDevice(&prev);

@@ -71,7 +71,8 @@ def segment_array(segs):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_size_t), ("max_batch_rows", ctypes.c_int),
-                ("max_inflight_batches", ctypes.c_int), ("streams_per_model", ctypes.c_int)]
+                ("max_inflight_batches", ctypes.c_int), ("streams_per_model", ctypes.c_int),
+                ("batch_min_rows", ctypes.c_int), ("batch_wait_us", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -304,10 +305,11 @@ class Server:
     (tabnet_server_*).  Inputs are numpy arrays kept alive until release."""
 
     def __init__(self, models, device_bytes=1 << 30, max_batch_rows=65536, max_inflight_batches=32,
-                 streams_per_model=8):
+                 streams_per_model=8, batch_min_rows=512, batch_wait_us=200):
         self.models = list(models)
         arr = (ctypes.c_void_p * len(self.models))(*[m.handle for m in self.models])
-        cfg = ServerConfig(device_bytes, max_batch_rows, max_inflight_batches, streams_per_model)
+        cfg = ServerConfig(device_bytes, max_batch_rows, max_inflight_batches, streams_per_model, batch_min_rows,
+                           batch_wait_us)
         h = ctypes.c_void_p()
         _check(lib().tabnet_server_create(arr, len(self.models), ctypes.byref(cfg), ctypes.byref(h)),
                "tabnet_server_create")
