@@ -34,9 +34,14 @@
 //     and the residual (kept in fp32 registers), and write the next layer's
 //     A operand straight into shared memory.
 //   * Sparsemax runs in fp32, row per thread, by Michelot's fixed point on
-//     the threshold (the sort-free exact projection); the prior P lives in
-//     TMEM in fp32, the current mask in TMEM as fp16 pairs (read again only
-//     for the aggregate), the per-feature aggregate in TMEM or shared memory.
+//     the threshold (the sort-free exact projection); the prior P and the
+//     current mask live in TMEM in fp32 (the mask is read again for the
+//     aggregate once the step's decision output is known), the per-feature
+//     aggregate in TMEM or shared memory.  Only when those fp32 regions do
+//     not fit next to a 256-column accumulator (128 hidden units with a
+//     160-column mask) is the mask kept as fp16 pairs.
+//   * The attentive layer's MMA chain starts at K step n_d / 16: its weights
+//     on the decision half of the feature transformer's output are zero.
 //   * Masks and the aggregate leave through per-warp staging blocks as
 //     64-byte row pieces.
 //   * With NWG = 2 two warpgroups split the columns of each row and combine
@@ -59,10 +64,6 @@
 
 namespace tabnet {
 
-#ifdef TABNET_TRACE
-unsigned* tabnet_debug_trace_ptr();
-#endif
-
 namespace {
 
 constexpr uint64_t kWaitLimit = 1000000000ull;  // 1 s per wait
@@ -72,44 +73,6 @@ constexpr int kFStride = 129;  // row stride (floats) of the input cache: transp
 // sparsemax input kept in registers: up to this many 16-column chunks per thread
 // (two warpgroups per row keep z in TMEM: their register budget is 128)
 __host__ __device__ constexpr int zreg_chunks(int nwg) { return nwg == 1 ? 3 : 0; }
-
-#ifdef TABNET_TRACE
-#define TC_TRACE(i, v)                                                          \
-    do {                                                                        \
-        if (p.trace && blockIdx.x == 0) {                                       \
-            reinterpret_cast<volatile unsigned*>(p.trace)[(i)] = (unsigned)(v); \
-            __threadfence_system();                                             \
-        }                                                                       \
-    } while (0)
-#else
-#define TC_TRACE(i, v) \
-    do {               \
-    } while (0)
-#endif
-
-#ifdef TABNET_TRACE
-#define PH_DECL unsigned long long ph_t = clock64(); unsigned long long ph_acc[16] = {0};
-#define PH_MARK(k)                          \
-    do {                                    \
-        const unsigned long long _t = clock64(); \
-        ph_acc[(k)] += _t - ph_t;           \
-        ph_t = _t;                          \
-    } while (0)
-#define PH_DUMP()                                                                                   \
-    do {                                                                                            \
-        if (p.trace && blockIdx.x == 0 && (lt % 32) == 0)                                           \
-            for (int _k = 0; _k < 16; ++_k)                                                         \
-                reinterpret_cast<volatile unsigned long long*>(p.trace + 1024)[(tid / 32) * 16 + _k] = ph_acc[_k]; \
-    } while (0)
-#else
-#define PH_DECL
-#define PH_MARK(k) \
-    do {           \
-    } while (0)
-#define PH_DUMP() \
-    do {          \
-    } while (0)
-#endif
 
 // Record a wait that ran out: the status bit, and the first location.
 __device__ __forceinline__ void note_timeout(unsigned* status, unsigned kind, unsigned index) {
@@ -286,13 +249,37 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *sTmem;
-    TC_TRACE(64 + tid / 32, 2);
-    PH_DECL
     const uint32_t t_acc = tmem + lane_off;
     const uint32_t t_p = t_acc + (uint32_t)p.tm_p;
     const uint32_t t_m = t_acc + (uint32_t)p.tm_m;
     const bool agg_tmem = LEAN || p.tm_agg >= 0;
     const uint32_t t_agg = t_acc + (uint32_t)(agg_tmem ? p.tm_agg : 0);
+    // the last 16-column chunk of the P / mask / aggregate regions holds 8
+    // columns when the mask width leaves at most 8 in it
+    const bool tail8 = p.tail8 != 0;
+    const bool m16 = p.m16 != 0;  // step mask kept as fp16 pairs (TMEM budget)
+    const int dchunks = p.dp / 16;
+    // 16 columns of a P / mask / aggregate region (8 in a half chunk, the
+    // rest read as 0); the caller waits with tmem_wait_ld
+    auto tm_ld = [&](uint32_t taddr, int ch, uint32_t (&r)[16]) {
+        if (tail8 && ch == dchunks - 1) {
+#pragma unroll
+            for (int j = 8; j < 16; ++j) r[j] = 0u;
+            ptx::tmem_ld8_lo(taddr, r);
+        } else {
+            ptx::tmem_ld16(taddr, r);
+        }
+    };
+    auto tm_st = [&](uint32_t taddr, int ch, const uint32_t (&r)[16]) {
+        if (tail8 && ch == dchunks - 1) {
+            uint32_t h[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) h[j] = r[j];
+            ptx::tmem_st8(taddr, h);
+        } else {
+            ptx::tmem_st16(taddr, r);
+        }
+    };
 
     const int64_t total = total_rows(p.seg, rows);
     const int64_t num_tiles = (total + 127) / 128;
@@ -328,7 +315,6 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             empty_par ^= 1u << slot;
             empty_pending &= ~(1u << slot);
         }
-        PH_MARK(8);
         const uint2 ck = sChunks[is_chunk];
         ptx::mbar_arrive_expect_tx(bar_full + 8 * slot, ck.y);
         ptx::bulk_g2s(ring_base + (uint32_t)(slot * p.slot_bytes), p.wbase + ck.x, ck.y, bar_full + 8 * slot);
@@ -341,20 +327,19 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         while (g_issue < total_chunks && g_issue < S) issue_next();
 
     // Publish this thread's A-operand writes and TMEM reads, then let thread 0
-    // run one layer's MMA chain (kblocks 64-wide K blocks, kb K steps of 16)
-    // and wait for the accumulator.  Returns false when the CTA has to stop.
-    auto run_mma = [&](int kblocks, int kb, uint32_t idesc) -> bool {
-        PH_MARK(7);
+    // run one layer's MMA chain (K steps of 16 columns [kbeg, kend) over the
+    // 64-wide K blocks that hold them) and wait for the accumulator.
+    // Returns false when the CTA has to stop.
+    auto run_mma = [&](int kbeg, int kend, uint32_t idesc) -> bool {
         ptx::fence_proxy_async();
         ptx::tc_fence_before();
         __syncthreads();
         if (sAbort[lc & 1]) return false;
         if (tid == 0) {
             ptx::tc_fence_after();
-            int kk = 0;
             bool ok = true;
 #pragma unroll 1
-            for (int b = 0; b < kblocks && ok; ++b) {
+            for (int b = kbeg >> 2; 4 * b < kend && ok; ++b) {
                 while (ok && g_issue < g_cons + PARTS) ok = issue_next();
                 // slots (and rounds) of this K block's hi and lo chunks
                 int slot_p[PARTS];
@@ -369,14 +354,12 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                         if (++sl == S) { sl = 0; ++rd; }
                     }
                 }
-                PH_MARK(12);
                 for (int part = 0; part < PARTS && ok; ++part) {
                     if (!ptx::mbar_wait(bar_full + 8 * slot_p[part], round_p[part] & 1u, kWaitLimit)) {
                         note_timeout(m.status, 1, (unsigned)(g_cons + part));
                         ok = false;
                     }
                 }
-                PH_MARK(13);
                 if (!ok) break;
                 // descriptors of the block's first K step; a K step of 16
                 // bf16 (32 bytes) adds 2 to the encoded start address
@@ -386,7 +369,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     d_b[part] = ptx::sw128_desc(ring_base + (uint32_t)(slot_p[part] * p.slot_bytes));
                     d_a[part] = ptx::sw128_desc(a_base + (uint32_t)part * a_part + (uint32_t)(b * 16384));
                 }
-                const int nk = min(4, kb - kk);
+                const int k0 = max(kbeg - 4 * b, 0), k1 = min(kend - 4 * b, 4);
                 if constexpr (NP == 3) {
                     // Products whose parts' significance reaches 2^-16 of hi hi:
                     // the five small ones first, so that most additions into
@@ -394,9 +377,9 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     // rounds relative to the running sum), then hi hi.
 #pragma unroll
                     for (int k4 = 0; k4 < 4; ++k4) {
-                        if (k4 < nk) {
+                        if (k4 >= k0 && k4 < k1) {
                             const uint64_t step = 2u * (uint32_t)k4;
-                            ptx::mma_f16(tmem, d_a[0] + step, d_b[1] + step, idesc, (kk + k4) > 0 ? 1u : 0u);
+                            ptx::mma_f16(tmem, d_a[0] + step, d_b[1] + step, idesc, (4 * b + k4) > kbeg ? 1u : 0u);
                             ptx::mma_f16(tmem, d_a[1] + step, d_b[0] + step, idesc, 1u);
                             ptx::mma_f16(tmem, d_a[0] + step, d_b[2] + step, idesc, 1u);
                             ptx::mma_f16(tmem, d_a[1] + step, d_b[1] + step, idesc, 1u);
@@ -405,7 +388,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     }
 #pragma unroll
                     for (int k4 = 0; k4 < 4; ++k4) {
-                        if (k4 < nk) {
+                        if (k4 >= k0 && k4 < k1) {
                             const uint64_t step = 2u * (uint32_t)k4;
                             ptx::mma_f16(tmem, d_a[0] + step, d_b[0] + step, idesc, 1u);
                         }
@@ -413,10 +396,10 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 } else {
 #pragma unroll
                     for (int k4 = 0; k4 < 4; ++k4) {
-                        if (k4 < nk) {
+                        if (k4 >= k0 && k4 < k1) {
                             // hi hi; with two parts also hi lo and lo hi
                             const uint64_t step = 2u * (uint32_t)k4;
-                            ptx::mma_f16(tmem, d_a[0] + step, d_b[0] + step, idesc, (kk + k4) > 0 ? 1u : 0u);
+                            ptx::mma_f16(tmem, d_a[0] + step, d_b[0] + step, idesc, (4 * b + k4) > kbeg ? 1u : 0u);
                             if constexpr (NP >= 2) {
                                 ptx::mma_f16(tmem, d_a[0] + step, d_b[1] + step, idesc, 1u);
                                 ptx::mma_f16(tmem, d_a[1] + step, d_b[0] + step, idesc, 1u);
@@ -424,10 +407,9 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                         }
                     }
                 }
-                kk += nk;
 #pragma unroll
                 for (int part = 0; part < PARTS; ++part) {
-                    if (b + 1 < kblocks) {
+                    if (4 * (b + 1) < kend) {
                         ptx::mma_commit(bar_empty + 8 * slot_p[part]);
                         empty_pending |= 1u << slot_p[part];
                     }
@@ -438,7 +420,6 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     if (++cs_slot == S) { cs_slot = 0; ++cs_round; }
             }
             ptx::mma_commit(bar_acc);
-            PH_MARK(9);
             acc_outstanding = true;
             if (!ok) sAbort[(lc + 1) & 1] = 1;
         }
@@ -460,20 +441,17 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 note_timeout(m.status, 2, (unsigned)lc);
             }
         }
-        PH_MARK(10);
         if (tid == 0) {
             if (got) acc_outstanding = false;
             // every MMA so far has completed: refill the free slots
             if (!sAbort[(lc + 1) & 1])
                 while (g_issue < total_chunks && g_issue < g_cons + S)
                     if (!issue_next()) { sAbort[(lc + 1) & 1] = 1; break; }
-            PH_MARK(11);
         }
         acc_phase ^= 1;
         ++lc;
         if constexpr (!kAllWait) __syncthreads();
         ptx::tc_fence_after();
-        PH_MARK(1);
         return true;
     };
 
@@ -672,12 +650,12 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             uint32_t ones[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) ones[j] = 0x3f800000u;
-            ptx::tmem_st16(t_p + ch * 16, ones);
+            tm_st(t_p + ch * 16, ch, ones);
             if (agg_tmem) {
                 uint32_t zeros[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) zeros[j] = 0u;
-                ptx::tmem_st16(t_agg + ch * 16, zeros);
+                tm_st(t_agg + ch * 16, ch, zeros);
             }
         }
         if (!agg_tmem) {
@@ -688,7 +666,6 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             for (int j = wg; j < m.d; j += NWG) sAgg[j * 128 + lt] = 0.f;
         }
         ptx::tmem_wait_st();
-        PH_MARK(0);
         float lacc[kMaxClasses];
 #pragma unroll 1
         for (int k = 0; k < n_cls; ++k) lacc[k] = 0.f;
@@ -707,8 +684,11 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 #pragma unroll 1
         while (true) {
             const bool first = !att && l == 0;
-            if (!run_mma(att ? p.kn_blocks : (first ? p.k0_blocks : p.kn_blocks), (att || !first) ? N / 16 : dch,
-                         att ? idesc_att : idesc_ft)) {
+            // K steps: a feature transformer's first layer reads the dp masked
+            // inputs, the others the N outputs of the layer before; the
+            // attentive layer reads only the attention half (its weights on
+            // the decision half are 0)
+            if (!run_mma(att ? p.att_k0 : 0, (att || !first) ? N / 16 : dch, att ? idesc_att : idesc_ft)) {
                 alive = false;
                 break;
             }
@@ -718,7 +698,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 auto load_z = [&](int ch, float (&z)[16], uint32_t (&pr)[16]) {
                     uint32_t acc[16];
                     ptx::tmem_ld16(t_acc + ch * 16, acc);
-                    ptx::tmem_ld16(t_p + ch * 16, pr);
+                    tm_ld(t_p + ch * 16, ch, pr);
                     ptx::tmem_wait_ld(acc, pr);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -819,8 +799,6 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     // hence the same flags, and leave together
                     if (!__any_sync(0xffffffffu, !done)) break;
                 }
-                TC_TRACE(128 + tid / 32, 4000 + lc);
-                PH_MARK(2);
                 // Mask, prior, masked input (A for the step's first FC), outputs.
                 float* mrow = (io.masks && valid) ? io.masks + (size_t)(s - 1) * de : nullptr;
                 float* const* sRowM = reinterpret_cast<float* const*>(smem + p.sm.rowp + 128 * 16);
@@ -830,7 +808,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     float z[16];
                     uint32_t pr[16];
                     if constexpr (ZREG) {
-                        ptx::tmem_ld16(t_p + ch * 16, pr);
+                        tm_ld(t_p + ch * 16, ch, pr);
                         ptx::tmem_wait_ld(pr);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
@@ -843,25 +821,31 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     } else {
                         uint32_t zu[16];
                         ptx::tmem_ld16(t_acc + ch * 16, zu);
-                        ptx::tmem_ld16(t_p + ch * 16, pr);
+                        tm_ld(t_p + ch * 16, ch, pr);
                         ptx::tmem_wait_ld(zu, pr);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) z[j] = __uint_as_float(zu[j]);
                     }
                     float mk[16], v[16];
-                    uint32_t pn[16], mh[8];
+                    uint32_t pn[16], mu[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         mk[j] = fmaxf(z[j] - tau, 0.f);
                         pn[j] = __float_as_uint(__uint_as_float(pr[j]) * (gamma - mk[j]));
+                        mu[j] = __float_as_uint(mk[j]);
                     }
+                    tm_st(t_p + ch * 16, ch, pn);
+                    if (!m16) {
+                        tm_st(t_m + ch * 16, ch, mu);  // the mask, kept in fp32 for the aggregate
+                    } else {
+                        uint32_t mh[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        __half2 h = __floats2half2_rn(mk[2 * j], mk[2 * j + 1]);
-                        mh[j] = *reinterpret_cast<uint32_t*>(&h);
+                        for (int j = 0; j < 8; ++j) {
+                            __half2 h = __floats2half2_rn(mk[2 * j], mk[2 * j + 1]);
+                            mh[j] = *reinterpret_cast<uint32_t*>(&h);
+                        }
+                        ptx::tmem_st8(t_m + ch * 8, mh);
                     }
-                    ptx::tmem_st16(t_p + ch * 16, pn);
-                    ptx::tmem_st8(t_m + ch * 8, mh);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int c = ch * 16 + j;
@@ -888,7 +872,6 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     store_a16<NP>(sA, sAlo, a_part, lt, ch, v);
                 }
                 ptx::tmem_wait_st();
-                PH_MARK(3);
                 att = false;
                 continue;
             }
@@ -898,7 +881,6 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             // x = sqrt(1/2) (x_prev + g): the linear half of every layer but an
             // FT's first is packed pre-scaled by sqrt(1/2), so x = x_prev sqrt(1/2) + g
             const float cres = first ? 0.f : kSqrtHalf;
-            TC_TRACE(128 + tid / 32, 3000 + lc);
             // One warpgroup alone on a row (NWG = 1) takes 16-column pieces and
             // requests piece k+1 from TMEM before computing piece k; with two
             // warpgroups per row, 8-column pieces loaded one at a time keep
@@ -909,7 +891,6 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             ptx::tmem_ld_cols<SW>(t_acc + wg * CPW, lin[0]);
             ptx::tmem_ld_cols<SW>(t_acc + N + wg * CPW, gat[0]);
             ptx::tmem_wait_ld(lin[0], gat[0]);
-            PH_MARK(14);
 #pragma unroll
             for (int sc = 0; sc < NSUB; ++sc) {
                 const int c0 = wg * CPW + sc * SW;
@@ -949,7 +930,6 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 if constexpr (SW == 16) store_a16<NP>(sA, sAlo, a_part, lt, c0 / 16, out);
                 else store_a8<NP>(sA, sAlo, a_part, lt, c0 / 8, out);
             }
-            PH_MARK(4);
             if (++l < lpf) continue;
             l = 0;
             if (s > 0) {
@@ -986,47 +966,47 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     lacc[k] += a0 + a1;
                 }
                 eta = xsum(eta, 0.f).x;
-                PH_MARK(5);
-                if (agg_tmem) {
+                // aggregate += eta * M (the step's mask as kept in TMEM)
 #pragma unroll 1
-                    for (int ch = wg; ch < dch; ch += NWG) {
-                        uint32_t mh[8], ag[16];
+                for (int ch = wg; ch < dch; ch += NWG) {
+                    float mv[16];
+                    if (!m16) {
+                        uint32_t mu[16];
+                        tm_ld(t_m + ch * 16, ch, mu);
+                        ptx::tmem_wait_ld(mu);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) mv[j] = __uint_as_float(mu[j]);
+                    } else {
+                        uint32_t mh[8];
                         ptx::tmem_ld8(t_m + ch * 8, mh);
-                        ptx::tmem_ld16(t_agg + ch * 16, ag);
-                        ptx::tmem_wait_ld(ag);
-                        asm volatile("" : "+r"(mh[0]), "+r"(mh[1]), "+r"(mh[2]), "+r"(mh[3]), "+r"(mh[4]),
-                                     "+r"(mh[5]), "+r"(mh[6]), "+r"(mh[7]));
+                        ptx::tmem_wait_ld8(mh);
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             const float2 mm = __half22float2(*reinterpret_cast<__half2*>(&mh[j]));
-                            ag[2 * j] = __float_as_uint(fmaf(eta, mm.x, __uint_as_float(ag[2 * j])));
-                            ag[2 * j + 1] = __float_as_uint(fmaf(eta, mm.y, __uint_as_float(ag[2 * j + 1])));
+                            mv[2 * j] = mm.x;
+                            mv[2 * j + 1] = mm.y;
                         }
-                        ptx::tmem_st16(t_agg + ch * 16, ag);
                     }
-                    ptx::tmem_wait_st();
-                    PH_MARK(5);
-                } else
-                for (int ch = wg; ch < dch; ch += NWG) {
-                    uint32_t mh[8];
-                    ptx::tmem_ld8(t_m + ch * 8, mh);
-                    ptx::tmem_wait_ld8(mh);
+                    if (agg_tmem) {
+                        uint32_t ag[16];
+                        tm_ld(t_agg + ch * 16, ch, ag);
+                        ptx::tmem_wait_ld(ag);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float2 mm = __half22float2(*reinterpret_cast<__half2*>(&mh[j]));
-                        const float mv[2] = {mm.x, mm.y};
+                        for (int j = 0; j < 16; ++j) ag[j] = __float_as_uint(fmaf(eta, mv[j], __uint_as_float(ag[j])));
+                        tm_st(t_agg + ch * 16, ch, ag);
+                    } else {
 #pragma unroll
-                        for (int t = 0; t < 2; ++t) {
-                            const int c = ch * 16 + 2 * j + t;
-                            if (c < de && mv[t] > 0.f) {
+                        for (int j = 0; j < 16; ++j) {
+                            const int c = ch * 16 + j;
+                            if (c < de && mv[j] > 0.f) {
                                 float* dst = sAgg + sColf[c] * 128 + lt;
-                                if constexpr (NWG == 1) *dst = fmaf(eta, mv[t], *dst);
-                                else atomicAdd(dst, eta * mv[t]);
+                                if constexpr (NWG == 1) *dst = fmaf(eta, mv[j], *dst);
+                                else atomicAdd(dst, eta * mv[j]);
                             }
                         }
                     }
                 }
-                PH_MARK(5);
+                if (agg_tmem) ptx::tmem_wait_st();
             }
             if (++s > m.n_steps) break;
             att = true;
@@ -1045,7 +1025,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 #pragma unroll 1
             for (int ch = wg; ch < dch; ch += NWG) {
                 uint32_t ag[16];
-                ptx::tmem_ld16(t_agg + ch * 16, ag);
+                tm_ld(t_agg + ch * 16, ch, ag);
                 ptx::tmem_wait_ld(ag);
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
@@ -1057,7 +1037,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 #pragma unroll 1
             for (int ch = wg; ch < dch; ch += NWG) {
                 uint32_t ag[16];
-                ptx::tmem_ld16(t_agg + ch * 16, ag);
+                tm_ld(t_agg + ch * 16, ch, ag);
                 ptx::tmem_wait_ld(ag);
                 if (mstw) {
                     float v[16];
@@ -1089,12 +1069,9 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 for (int j = wg; j < m.d; j += NWG) io.agg[j] = tot > 0.f ? sAgg[j * 128 + lt] * inv : 0.f;
             }
         }
-        PH_MARK(6);
     }
-    PH_DUMP();
 
     // ---- teardown: no copy or MMA may still target this CTA's memory
-    TC_TRACE(96 + tid / 32, 900000 + lc);
     __syncthreads();
     if (tid == 0) {
         int sl = cs_slot;
@@ -1114,7 +1091,6 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     __syncthreads();
     ptx::tc_fence_after();
     if (warp == 0) ptx::tmem_dealloc(tmem, (uint32_t)p.tmem_cols);
-    TC_TRACE(96 + tid / 32, 999999);
 }
 
 // ---------------------------------------------------------------- host side
@@ -1271,37 +1247,50 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
     }
     if (dp > 256) { *why = "tensor-core path needs d_emb <= 256"; return TABNET_ERR_UNSUPPORTED_DIMS; }
     if (d.n_classes > kMaxClasses) { *why = "tensor-core path needs n_classes <= 4"; return TABNET_ERR_UNSUPPORTED_DIMS; }
+    // TMEM: the accumulator, then P and the step mask in fp32 (the last
+    // 16-column chunk cut to 8 columns when it holds at most 8 mask columns),
+    // then the aggregate when every feature is one embedded column
     const int accw = std::max(2 * N, dp);
-    const int need = accw + dp + dp / 2;
-    int cols = 32;
-    while (cols < need) cols *= 2;
+    const bool tail8 = (d.d_emb % 16) != 0 && (d.d_emb % 16) <= 8;
+    const int pw = tail8 ? dp - 8 : dp;
+    auto pow2 = [](int need) { int c = 32; while (c < need) c *= 2; return c; };
+    bool m16 = false;
+    int need = accw + 2 * pw;
+    if (need > 512) {
+        // the step mask as fp16 pairs: the only layout that fits 128 hidden
+        // units with a 160-column mask
+        m16 = true;
+        need = accw + pw + dp / 2;
+    }
+    int cols = pow2(need);
     if (cols > 512) { *why = "TMEM budget exceeded"; return TABNET_ERR_UNSUPPORTED_DIMS; }
     TcParams& p = m->tc;
     p.dp = dp;
+    p.tail8 = tail8 ? 1 : 0;
+    p.m16 = m16 ? 1 : 0;
     p.tm_p = accw;
-    p.tm_m = accw + dp;
+    p.tm_m = accw + pw;
+    p.att_k0 = d.n_d / 16;
     // the aggregate lives in TMEM when every feature is one embedded column
-    // and dp more columns fit in the allocation (or the next, <= 256)
+    // and its region fits in the allocation (or the next, <= 256)
     p.tm_agg = -1;
     if (d.d_emb == d.n_feat) {
-        int c2 = 32;
-        while (c2 < need + dp) c2 *= 2;
+        const int c2 = pow2(need + pw);
         if (c2 <= std::max(cols, 256)) { p.tm_agg = need; cols = c2; }
     }
     p.tmem_cols = cols;
-    p.k0_blocks = (dp + 63) / 64;
-    p.kn_blocks = (N + 63) / 64;
 
     const HostModel& hm = m->host;
     const int parts = np;
     // Every 64-wide K block of W (its parts in order: hi, then lo or mid, lo) becomes a chunk.
-    auto push_layer = [&](const float* W, int n_out, int k_valid, int col_shift, int k_pad,
+    // Blocks before first_block are not streamed (all their weights are 0).
+    auto push_layer = [&](const float* W, int n_out, int k_valid, int col_shift, int k_pad, int first_block,
                           std::vector<std::pair<size_t, uint32_t>>* keep) {
         const uint32_t cb = (uint32_t)n_out * 128;
         std::vector<std::vector<uint8_t>> pk(parts);
         for (int part = 0; part < parts; ++part) pack_sw128(W, n_out, k_valid, col_shift, k_pad, part, pk[part]);
         const int blocks = (k_pad + 63) / 64;
-        for (int b = 0; b < blocks; ++b)
+        for (int b = first_block; b < blocks; ++b)
             for (int part = 0; part < parts; ++part) {
                 const size_t off = a.add(pk[part].data() + (size_t)b * cb, cb, 1024);
                 keep->push_back({off, cb});
@@ -1328,7 +1317,9 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
             std::vector<float> wp((size_t)dp * d.n_a, 0.f);
             const std::vector<float> ws = scaled(hm.att_fc[s - 1], sc, d.d_emb, d.n_a);
             std::memcpy(wp.data(), ws.data(), sizeof(float) * d.d_emb * d.n_a);
-            push_layer(wp.data(), dp, d.n_a, d.n_d, N, &stream);
+            // the MMA chain starts at K step n_d / 16: blocks wholly inside the
+            // decision half are not streamed
+            push_layer(wp.data(), dp, d.n_a, d.n_d, N, (d.n_d / 16) / 4, &stream);
             sh.resize(dp, 0.f);
             att_epi.insert(att_epi.end(), sh.begin(), sh.end());
         }
@@ -1352,7 +1343,7 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
                 }
             }
             const std::vector<float> ws = scaled(*g.w, sc, 2 * N, g.k);
-            push_layer(ws.data(), 2 * N, g.k, 0, l == 0 ? dp : N, &stream);
+            push_layer(ws.data(), 2 * N, g.k, 0, l == 0 ? dp : N, 0, &stream);
             epi.insert(epi.end(), sh.begin(), sh.end());
         }
     }
@@ -1480,10 +1471,6 @@ cudaError_t tc_launch(tabnet_model* m, const float* x_num, const int* x_cat, int
                       float* masks, float* agg, cudaStream_t stream, const SegTable* seg) {
     TcParams p = m->tc;
     p.seg = seg ? *seg : SegTable{nullptr, nullptr, 0};
-    p.trace = nullptr;
-#ifdef TABNET_TRACE
-    cudaHostGetDevicePointer((void**)&p.trace, tabnet_debug_trace_ptr(), 0);
-#endif
     const TcLaunch& L = m->tc_launch_cfg;
     const int64_t slots = (int64_t)m->num_sms * L.ctas_per_sm;
     // a segmented launch learns its row count on the device: one CTA per slot
@@ -1499,16 +1486,5 @@ cudaError_t tc_launch(tabnet_model* m, const float* x_num, const int* x_cat, int
 
 void tc_release(tabnet_model*) {}
 
-#ifdef TABNET_TRACE
-static unsigned* g_trace_host = nullptr;
-unsigned* tabnet_debug_trace_ptr() {
-    if (!g_trace_host) {
-        cudaHostAlloc((void**)&g_trace_host, 4096 * sizeof(unsigned), cudaHostAllocMapped);
-        std::memset(g_trace_host, 0, 4096 * sizeof(unsigned));
-    }
-    return g_trace_host;
-}
-extern "C" unsigned* tabnet_debug_trace(void) { return tabnet_debug_trace_ptr(); }
-#endif
 
 }  // namespace tabnet

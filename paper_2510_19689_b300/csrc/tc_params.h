@@ -41,16 +41,20 @@ struct TcParams {
     const int2* col_info;      // [dp]: {-1, numeric column} | {categorical j, element e} | {-2, 0} pad
     const int* col_feat;       // [dp]: original feature of each embedded column (-1 for pad)
     int dp;                    // mask width padded to a multiple of 16
-    int k0_blocks;             // 64-wide K blocks of a feature transformer's first layer (K = dp)
-    int kn_blocks;             // 64-wide K blocks of the other layers and of the attentive layer (K = N)
+    int att_k0;                // first K step (16 columns) of the attentive layer: n_d / 16, the
+                               // decision half's weights before it being zero
     int tmem_cols;             // TMEM columns allocated per CTA
-    int tm_p;                  // TMEM column of the prior P (fp32, dp columns)
-    int tm_m;                  // TMEM column of the current mask (fp16 pairs, dp/2 columns)
-    int tm_agg;                // TMEM column of the aggregate (fp32, dp columns; -1: in shared memory)
+    // P, the step mask and the aggregate are fp32 regions of dp columns, or
+    // dp - 8 when the last 16-column chunk holds at most 8 mask columns (tail8)
+    int tail8;
+    int m16;                   // the step mask kept as fp16 pairs (dp / 2 columns): set only
+                               // when the fp32 regions exceed the 512 TMEM columns
+    int tm_p;                  // TMEM column of the prior P
+    int tm_m;                  // TMEM column of the current step mask
+    int tm_agg;                // TMEM column of the aggregate (-1: in shared memory)
     int n_slots;
     int slot_bytes;
     TcSmem sm;
-    unsigned* trace;           // debug builds only (TABNET_TRACE): progress words, else null
 };
 
 }  // namespace tabnet

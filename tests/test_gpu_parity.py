@@ -2,11 +2,16 @@
 
 The method is TabNet inference as the paper deploys it (Sec. IV-A; masks
 returned per call, Sec. III-B).  Tolerances:
-  * fp32 (FFMA) path: |logit - ref| <= 1e-5 * max(|ref|, 1) (the stated
-    bar); masks have no stated bar: each nonzero entry z - tau carries about
-    |z| * 2^-21 of fp32 rounding with |z| up to ~100 on the lognormal inputs,
-    summed over the support of every step, so per-row L1 over all steps
-    <= 5e-4 and aggregate per-row L1 <= 5e-4.
+  * fp32 (FFMA) path and the three-part split (bf16x6) tensor-core path:
+    |logit - ref| <= 1e-5 * max(|ref|, 1) (the stated bar).  Masks and the
+    aggregate have no stated bar; each nonzero mask entry z - tau carries a
+    few units of fp32 rounding of |z| (|z| up to ~100 on the lognormal
+    inputs), so the worst rows are those whose support sits next to a
+    near-tie.  On these seeded cases the worst per-row mask L1 over all
+    steps is 1.1e-4 (fp32, 35-input model) and 5.4e-5 (bf16x6), and the
+    worst aggregate L1 1.5e-5 (the aggregate is summed from the fp32 masks
+    in both): gated at 2e-4 / 1e-4 for the masks and 5e-5 for the
+    aggregate, about 2x the worst case.
   * bf16x3 (split-bf16 tensor-core) path, the stated bf16 bar:
     |logit - ref| <= 2e-2; argmax agreement >= 99.9 %; per-row L1 of the
     mask error summed over all steps <= 2e-2 (every row); aggregate per-row
@@ -34,11 +39,11 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {
-    "fp32": dict(logit_rel=1e-5, mask_l1=5e-4, agg_l1=5e-4, argmax=1.0),
+    "fp32": dict(logit_rel=1e-5, mask_l1=2e-4, agg_l1=5e-5, argmax=1.0),
     "bf16x3": dict(logit_abs=2e-2, mask_l1=2e-2, agg_l1=2e-2, argmax=0.999),
     "bf16": dict(logit_abs=0.3, mask_l1_mean=0.2, mask_l1_p99=2.0, agg_l1_mean=0.2, argmax=0.97),
     # the three-part split is held to the float32 bar
-    "bf16x6": dict(logit_rel=1e-5, mask_l1=5e-4, agg_l1=5e-4, argmax=1.0),
+    "bf16x6": dict(logit_rel=1e-5, mask_l1=1e-4, agg_l1=5e-5, argmax=1.0),
 }
 PRECISIONS = ["fp32", "bf16x3", "bf16", "bf16x6"]
 
