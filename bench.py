@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16", "bf16x6", "fp32"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16", "bf16x6", "fp8", "fp32"])
     ap.add_argument("--no-extras", action="store_true", help="skip the comparison arms")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shape")
     return ap.parse_args()

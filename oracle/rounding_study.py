@@ -37,10 +37,12 @@ oracle is the effect of the operand rounding alone:
 * ``int8w``  weights alone as in ``int8``, FC inputs exact (a weight-only
   INT8 variant, the best any INT8-weight kernel could do).
 
-These tables are why the library offers split-bf16 with all three products
-(it meets the stated bf16 tolerances; neither two-product form does) and no
-FP8 path (E4M3 operands move the sparsemax supports
-of most rows).
+These tables are why the library's default bf16 mode is split-bf16 with all
+three products (it meets the stated bf16 tolerances; neither two-product form
+does), and they state the error of its single-rounding modes: plain bf16 and
+FP8 E4M3 (whose operands move the sparsemax supports of most rows).  The GPU
+tests also hold those two kernels element by element to ``forward_rounded``
+in the matching mode.
 """
 from __future__ import annotations
 

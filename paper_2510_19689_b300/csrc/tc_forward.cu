@@ -1,6 +1,6 @@
 // TabNet forward with the fully connected layers on the 5th-generation
-// tensor cores (tcgen05, sm_103a): the bf16, split-bf16 and three-part
-// (float32-accurate) precision modes.
+// tensor cores (tcgen05, sm_103a): the bf16, split-bf16, three-part
+// (float32-accurate) and FP8 E4M3 precision modes.
 //
 // One CTA owns a tile of 128 rows for the whole forward pass: the embedding
 // and input BN, the step-0 feature transformer, then per decision step the
@@ -20,11 +20,15 @@
 //     memory (TMEM lane = row).  In split mode both operands are carried as
 //     hi + lo bf16 pairs and each K step issues hi*hi, hi*lo and lo*hi; with
 //     three parts (hi, lo, lo2) the five products down to 2^-16 of hi*hi go
-//     first and hi*hi last.  One phase loop walks a tile's layers, so there
-//     is one MMA issue site.
+//     first and hi*hi last.  In FP8 mode (kind::f8f6f4, 32-element K steps)
+//     the weights are E4M3 scaled per output channel (amax / 448, quantized
+//     on the host) and every FC input is E4M3 scaled per row (amax / 448 of
+//     the row's K inputs -- of the attention half for the attentive layer);
+//     the epilogue multiplies the accumulator by both scales.  One phase
+//     loop walks a tile's layers, so there is one MMA issue site.
 //   * Weights stream from L2 through a ring of shared-memory slots filled by
-//     1-D bulk async copies (TMA engine), one part of a 64-wide K block per
-//     slot, pre-swizzled by the host.  Thread 0 issues copies and MMAs; each
+//     1-D bulk async copies (TMA engine), one part of a K block (128 bytes a
+//     row: 64 bf16 or 128 e4m3 elements) per slot, pre-swizzled by the host.  Thread 0 issues copies and MMAs; each
 //     slot has a "full" barrier (copy landed); a slot read by a layer's last
 //     K block is free once the accumulator barrier fires, earlier blocks'
 //     slots get their own "empty" commit.
@@ -81,19 +85,15 @@ __device__ __forceinline__ void note_timeout(unsigned* status, unsigned kind, un
 }
 
 // sigmoid(x) = 1 / (1 + 2^(-x log2 e)) with the ex2/rcp approximations
-// (about 2^-21 relative): the split mode's gate.  The argument is y =
-// -x log2 e, already scaled by the packed gate weights and shifts.
+// (about 2^-21 relative): the gate of every tensor-core mode, so that a mode
+// differs from float32 arithmetic only by its operand rounding.  The
+// argument is y = -x log2 e, already scaled by the packed gate weights and
+// shifts.
 __device__ __forceinline__ float sigmoid_from_log2(float y) {
     float e, r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
     return r;
-}
-
-// sigmoid(x) = (1 + tanh(x / 2)) / 2 with tanh.approx (about 2^-11): the
-// plain bf16 mode's gate, one MUFU operation.
-__device__ __forceinline__ float sigmoid_fast(float x) {
-    return fmaf(0.5f, ptx::tanh_approx(0.5f * x), 0.5f);
 }
 
 // Byte offset of 16-byte unit q (0..7) of row r inside a 128-row x 64-column
@@ -168,6 +168,24 @@ __device__ __forceinline__ void store_a8(uint8_t* sA, uint8_t* sAlo, uint32_t pa
     (void)part_bytes;
 }
 
+// Row r, K columns [16 ch, 16 ch + 16) of an FP8 E4M3 A operand: v * inv
+// rounded to nearest even and saturated at +-448, one byte per element (a
+// 128-element K block is one 128-byte row of the 128B-swizzled layout).
+__device__ __forceinline__ void store_a16_e4m3(uint8_t* sA, int r, int ch, const float (&v)[16], float inv) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        w[j] = (uint32_t)ptx::cvt_e4m3x2(v[4 * j] * inv, v[4 * j + 1] * inv) |
+               ((uint32_t)ptx::cvt_e4m3x2(v[4 * j + 2] * inv, v[4 * j + 3] * inv) << 16);
+    *reinterpret_cast<uint4*>(sA + (uint32_t)((ch >> 3) * 16384) + sw128_off(r, ch & 7)) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Zero K columns [16 ch, 16 ch + 16) of row r of an FP8 A operand (the
+// padding a 32-element K step reads past a width that is 16 mod 32).
+__device__ __forceinline__ void zero_a16_e4m3(uint8_t* sA, int r, int ch) {
+    *reinterpret_cast<uint4*>(sA + (uint32_t)((ch >> 3) * 16384) + sw128_off(r, ch & 7)) = make_uint4(0u, 0u, 0u, 0u);
+}
+
 // Folded-BN vectors: staged in shared memory (epi_s != 0, a shared address)
 // or read through the read-only path from global memory.
 template <bool STAGED>
@@ -187,8 +205,9 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     constexpr int THREADS = 128 * NWG;
     constexpr int CPW = N / NWG;  // GLU output columns per warpgroup
     constexpr int RCH = CPW / 16;  // 16-column chunks per thread
+    constexpr bool FP8 = NP == 0;         // FP8 E4M3 operands (one 8-bit part, per-row and per-channel scales)
     constexpr bool SPLIT = NP >= 2;       // operands carried in several bf16 parts
-    constexpr int PARTS = NP;             // weight chunks (parts) per 64-wide K block
+    constexpr int PARTS = FP8 ? 1 : NP;   // weight chunks (parts) per K block
     constexpr int kZregChunks = zreg_chunks(NWG);
     static_assert(CPW % 16 == 0, "each warpgroup takes whole 16-column chunks");
 
@@ -393,6 +412,15 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                             ptx::mma_f16(tmem, d_a[0] + step, d_b[0] + step, idesc, 1u);
                         }
                     }
+                } else if constexpr (FP8) {
+                    // 32 e4m3 elements (32 bytes) per K step
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        if (k4 >= k0 && k4 < k1) {
+                            const uint64_t step = 2u * (uint32_t)k4;
+                            ptx::mma_f8(tmem, d_a[0] + step, d_b[0] + step, idesc, (4 * b + k4) > kbeg ? 1u : 0u);
+                        }
+                    }
                 } else {
 #pragma unroll
                     for (int k4 = 0; k4 < 4; ++k4) {
@@ -517,11 +545,15 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 
     const int de = m.de, dch = p.dp / 16, n_d = m.n_d, n_cls = m.n_classes;
     const float gamma = m.gamma;
-    const uint32_t idesc_ft = ptx::idesc_bf16(2 * N);
-    const uint32_t idesc_att = ptx::idesc_bf16(p.dp);
+    const uint32_t idesc_ft = FP8 ? ptx::idesc_e4m3(2 * N) : ptx::idesc_bf16(2 * N);
+    const uint32_t idesc_att = FP8 ? ptx::idesc_e4m3(p.dp) : ptx::idesc_bf16(p.dp);
+    // FP8: per-output-channel weight scales, indexed like the BN shifts
+    const int esc = p.epi_sc;
     const int lpf = m.layers_per_ft;
     const int n_ft_layers = (m.n_steps + 1) * lpf;
 
+    // FP8: scale of the current A operand's row (amax / 448 of what was stored)
+    float sa = 1.f;
     bool alive = true;
     for (int64_t tile = blockIdx.x; tile < num_tiles && alive; tile += gridDim.x) {
         const RowIO io = row_io(p.seg, m, tile * 128 + lt, total, x_num, x_cat, logits, masks, agg_out);
@@ -638,15 +670,34 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             }
             __syncthreads();
         }
+        // FP8: the row's scale is amax(f) / 448 (the first pass), then f is
+        // stored scaled by its inverse
+        float inv = 1.f;
+        if constexpr (FP8) {
+            float amax = 0.f;
+#pragma unroll 1
+            for (int ch = wg; ch < dch; ch += NWG) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int c = ch * 16 + j;
+                    amax = fmaxf(amax, fabsf(has_f ? (c < de ? fc[c * kFStride + lt] : 0.f) : f_value(c, valid)));
+                }
+            }
+            amax = xsummax(0.f, amax).y;
+            sa = amax > 0.f ? amax / 448.f : 1.f;
+            inv = amax > 0.f ? 448.f / amax : 1.f;
+            if (wg == 0 && (dch & 1)) zero_a16_e4m3(sA, lt, dch);
+        }
 #pragma unroll 1
         for (int ch = wg; ch < dch; ch += NWG) {
             float v[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int c = ch * 16 + j;
-                v[j] = has_f ? (c < de ? fc[c * kFStride + lt] : 0.f) : f_value(c, valid);
+                v[j] = has_f ? (c < de ? fc[c * kFStride + lt] : 0.f) : f_value(c, valid && !FP8);
             }
-            store_a16<NP>(sA, sAlo, a_part, lt, ch, v);
+            if constexpr (FP8) store_a16_e4m3(sA, lt, ch, v, inv);
+            else store_a16<NP>(sA, sAlo, a_part, lt, ch, v);
             uint32_t ones[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) ones[j] = 0x3f800000u;
@@ -688,7 +739,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             // inputs, the others the N outputs of the layer before; the
             // attentive layer reads only the attention half (its weights on
             // the decision half are 0)
-            if (!run_mma(att ? p.att_k0 : 0, (att || !first) ? N / 16 : dch, att ? idesc_att : idesc_ft)) {
+            if (!run_mma(att ? p.att_k0 : 0, (att || !first) ? p.ks_n : p.ks_0, att ? idesc_att : idesc_ft)) {
                 alive = false;
                 break;
             }
@@ -704,11 +755,16 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     for (int q = 0; q < 4; ++q) {
                         const float4 b = ld_epi<LEAN>(epi, epi_s, ash + ch * 16 + 4 * q);
                         const float bv[4] = {b.x, b.y, b.z, b.w};
+                        float wv[4] = {1.f, 1.f, 1.f, 1.f};
+                        if constexpr (FP8) {
+                            const float4 w = ld_epi<LEAN>(epi, epi_s, esc + ash + ch * 16 + 4 * q);
+                            wv[0] = sa * w.x; wv[1] = sa * w.y; wv[2] = sa * w.z; wv[3] = sa * w.w;
+                        }
 #pragma unroll
                         for (int t = 0; t < 4; ++t) {
                             const int j = 4 * q + t;
-                            z[j] = (ch * 16 + j < de) ? (__uint_as_float(acc[j]) + bv[t]) * __uint_as_float(pr[j])
-                                                      : -INFINITY;
+                            const float u = FP8 ? fmaf(__uint_as_float(acc[j]), wv[t], bv[t]) : __uint_as_float(acc[j]) + bv[t];
+                            z[j] = (ch * 16 + j < de) ? u * __uint_as_float(pr[j]) : -INFINITY;
                         }
                     }
                 };
@@ -801,6 +857,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 }
                 // Mask, prior, masked input (A for the step's first FC), outputs.
                 float* mrow = (io.masks && valid) ? io.masks + (size_t)(s - 1) * de : nullptr;
+                float vamax = 0.f;  // FP8: amax of the row's masked input
                 float* const* sRowM = reinterpret_cast<float* const*>(smem + p.sm.rowp + 128 * 16);
 #pragma unroll 1
                 for (int il = 0; wg + il * NWG < dch; ++il) {
@@ -855,6 +912,17 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                             v[j] = (c < de && mk[j] > 0.f) ? mk[j] * f_value(c, false) : 0.f;
                         }
                     }
+                    if constexpr (FP8) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) vamax = fmaxf(vamax, fabsf(v[j]));
+                        if constexpr (!ZREG) {
+                            // v replaces this chunk's z in TMEM until the row's scale is known
+                            uint32_t vu[16];
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) vu[j] = __float_as_uint(v[j]);
+                            ptx::tmem_st16(t_acc + ch * 16, vu);
+                        }
+                    }
                     if (mstw) {
                         stage_store(sRowM, (size_t)(s - 1) * de + ch * 16, min(16, de - ch * 16), mk);
                     } else if (mrow) {
@@ -869,9 +937,40 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                                 if (ch * 16 + j < de) mrow[ch * 16 + j] = mk[j];
                         }
                     }
-                    store_a16<NP>(sA, sAlo, a_part, lt, ch, v);
+                    if constexpr (!FP8) store_a16<NP>(sA, sAlo, a_part, lt, ch, v);
                 }
                 ptx::tmem_wait_st();
+                if constexpr (FP8) {
+                    // the masked input scaled by its row's amax / 448
+                    vamax = xsummax(0.f, vamax).y;
+                    sa = vamax > 0.f ? vamax / 448.f : 1.f;
+                    const float vinv = vamax > 0.f ? 448.f / vamax : 1.f;
+#pragma unroll 1
+                    for (int il = 0; wg + il * NWG < dch; ++il) {
+                        const int ch = wg + il * NWG;
+                        float v[16];
+                        if constexpr (ZREG) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                float zz = zr[0][j];
+#pragma unroll
+                                for (int q = 1; q < kZregChunks; ++q)
+                                    if (il == q) zz = zr[q][j];
+                                const int c = ch * 16 + j;
+                                const float mkj = fmaxf(zz - tau, 0.f);
+                                v[j] = c < de ? mkj * ptx::ld_shared_f32(f_s + 4u * (uint32_t)(c * kFStride + lt)) : 0.f;
+                            }
+                        } else {
+                            uint32_t vu[16];
+                            ptx::tmem_ld16(t_acc + ch * 16, vu);
+                            ptx::tmem_wait_ld(vu);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(vu[j]);
+                        }
+                        store_a16_e4m3(sA, lt, ch, v, vinv);
+                    }
+                    if (wg == 0 && (dch & 1)) zero_a16_e4m3(sA, lt, dch);
+                }
                 att = false;
                 continue;
             }
@@ -879,8 +978,15 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             // ---- layer l of feature transformer s
             const int sh = (s * lpf + l) * 2 * N;  // float index of the layer's BN shift
             // x = sqrt(1/2) (x_prev + g): the linear half of every layer but an
-            // FT's first is packed pre-scaled by sqrt(1/2), so x = x_prev sqrt(1/2) + g
+            // FT's first is scaled by sqrt(1/2), so x = x_prev sqrt(1/2) + g;
+            // the gate half by -log2(e), the sigmoid's argument.  The shifts
+            // are stored scaled; with several bf16 parts the packed weights
+            // are too (the parts then carry the scaled weight to ~2^-24), with
+            // one part the weights are rounded unscaled and the accumulator
+            // takes the constant (cl, cg)
             const float cres = first ? 0.f : kSqrtHalf;
+            const float cl = (SPLIT || first) ? 1.f : kSqrtHalf;
+            const float cg = SPLIT ? 1.f : -1.44269504088896340736f;
             // One warpgroup alone on a row (NWG = 1) takes 16-column pieces and
             // requests piece k+1 from TMEM before computing piece k; with two
             // warpgroups per row, 8-column pieces loaded one at a time keep
@@ -912,13 +1018,23 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     const float4 hg = ld_epi<LEAN>(epi, epi_s, sh + N + c0 + 4 * q);
                     const float hlv[4] = {hl.x, hl.y, hl.z, hl.w};
                     const float hgv[4] = {hg.x, hg.y, hg.z, hg.w};
+                    // accumulator multipliers: the constant pre-scales (the weights
+                    // are packed as BN-folded and rounded, unscaled); in FP8 the row
+                    // and channel scales, which carry the pre-scales
+                    float wl[4] = {cl, cl, cl, cl}, wgt[4] = {cg, cg, cg, cg};
+                    if constexpr (FP8) {
+                        const float4 a = ld_epi<LEAN>(epi, epi_s, esc + sh + c0 + 4 * q);
+                        const float4 b = ld_epi<LEAN>(epi, epi_s, esc + sh + N + c0 + 4 * q);
+                        wl[0] = sa * a.x; wl[1] = sa * a.y; wl[2] = sa * a.z; wl[3] = sa * a.w;
+                        wgt[0] = sa * b.x; wgt[1] = sa * b.y; wgt[2] = sa * b.z; wgt[3] = sa * b.w;
+                    }
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
                         const int j = 4 * q + t;
                         float& r = res[(sc * SW + j) / 16][(sc * SW + j) % 16];
-                        const float ul = __uint_as_float(lin[cur][j]) + hlv[t];
-                        const float ug = __uint_as_float(gat[cur][j]) + hgv[t];
-                        const float g = ul * (SPLIT ? sigmoid_from_log2(ug) : sigmoid_fast(ug));
+                        const float ul = fmaf(__uint_as_float(lin[cur][j]), wl[t], hlv[t]);
+                        const float ug = fmaf(__uint_as_float(gat[cur][j]), wgt[t], hgv[t]);
+                        const float g = ul * sigmoid_from_log2(ug);
                         const float x = fmaf(r, cres, g);
                         r = x;
                         out[j] = x;
@@ -927,8 +1043,28 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 if constexpr (NWG == 1) {
                     if (sc + 1 < NSUB) ptx::tmem_wait_ld(lin[cur ^ 1], gat[cur ^ 1]);
                 }
-                if constexpr (SW == 16) store_a16<NP>(sA, sAlo, a_part, lt, c0 / 16, out);
-                else store_a8<NP>(sA, sAlo, a_part, lt, c0 / 8, out);
+                if constexpr (!FP8) {
+                    if constexpr (SW == 16) store_a16<NP>(sA, sAlo, a_part, lt, c0 / 16, out);
+                    else store_a8<NP>(sA, sAlo, a_part, lt, c0 / 8, out);
+                }
+            }
+            if constexpr (FP8) {
+                // the layer's outputs scaled by the row's amax / 448; the last
+                // layer of a feature transformer feeds only the attentive
+                // layer, which reads the attention half: its amax alone
+                const bool att_next = l == lpf - 1;
+                float amax = 0.f;
+#pragma unroll
+                for (int cc = 0; cc < RCH; ++cc)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (!att_next || wg * CPW + cc * 16 + j >= n_d) amax = fmaxf(amax, fabsf(res[cc][j]));
+                amax = xsummax(0.f, amax).y;
+                sa = amax > 0.f ? amax / 448.f : 1.f;
+                const float ginv = amax > 0.f ? 448.f / amax : 1.f;
+#pragma unroll
+                for (int cc = 0; cc < RCH; ++cc) store_a16_e4m3(sA, lt, wg * RCH + cc, res[cc], ginv);
+                if (wg == 0 && ((N / 16) & 1)) zero_a16_e4m3(sA, lt, N / 16);
             }
             if (++l < lpf) continue;
             l = 0;
@@ -1139,11 +1275,57 @@ void pack_sw128(const float* W, int n_out, int k_valid, int col_shift, int k_pad
     }
 }
 
+// FP8 E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; no
+// infinities, largest finite 448) nearest to x, ties to even, saturating.
+uint8_t e4m3_rne(double x) {
+    const uint8_t sign = x < 0 ? 0x80 : 0x00;
+    double a = std::fabs(x);
+    if (!(a < 448.0)) return sign | 0x7E;  // saturate (NaN inputs do not occur: weights are finite)
+    int e;
+    std::frexp(a, &e);                 // a = m 2^e, m in [0.5, 1)
+    const int binade = std::max(e - 1, -6);  // subnormals share the 2^-6 binade's spacing
+    const double step = std::ldexp(1.0, binade - 3);
+    const double q = std::nearbyint(a / step);  // round-half-even in the default mode
+    double v = q * step;
+    if (v >= 448.0) return sign | 0x7E;
+    if (v == 0.0) return sign;
+    int ev;
+    const double mv = std::frexp(v, &ev);  // v = mv 2^ev
+    const int E = ev - 1 + 7;               // biased exponent of 1.f x 2^(ev-1)
+    if (E <= 0) return sign | (uint8_t)std::lround(v / std::ldexp(1.0, -9));  // subnormal: v / 2^-9
+    const int mant = (int)std::lround((mv * 2.0 - 1.0) * 8.0);
+    return sign | (uint8_t)((E << 3) | mant);
+}
+
+// Pack W [n_out, k_valid] (row-major doubles; input column j at K index
+// j + col_shift) into ceil(k_pad / 128) blocks of n_out x 128 e4m3 bytes in
+// the 128B-swizzled K-major layout, each row scaled by its own amax / 448;
+// scale[n] = amax / 448 (1 for an all-zero row).
+void pack_e4m3(const double* W, int n_out, int k_valid, int col_shift, int k_pad, std::vector<uint8_t>& out,
+               std::vector<double>& scale) {
+    const int n_blocks = (k_pad + 127) / 128;
+    out.assign((size_t)n_blocks * n_out * 128, 0);
+    scale.assign(n_out, 1.0);
+    for (int n = 0; n < n_out; ++n) {
+        double amax = 0.0;
+        for (int j = 0; j < k_valid; ++j) amax = std::max(amax, std::fabs(W[(size_t)n * k_valid + j]));
+        if (amax > 0.0) scale[n] = amax / 448.0;
+        for (int k = 0; k < n_blocks * 128; ++k) {
+            const int src = k - col_shift;
+            if (src < 0 || src >= k_valid) continue;
+            const int b = k / 128, kk = k % 128;
+            const size_t off = (size_t)b * n_out * 128 + (size_t)(n >> 3) * 1024 + (n & 7) * 128 +
+                               ((((kk >> 4) ^ (n & 7)) & 7) << 4) + (kk & 15);
+            out[off] = e4m3_rne(W[(size_t)n * k_valid + src] / scale[n]);
+        }
+    }
+}
+
 int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
 struct Variant {
     int N, nwg;
-    int np;  // bf16 parts per operand: 1 (bf16), 2 (split-bf16), 3 (three-part split)
+    int np;  // bf16 parts per operand: 1 (bf16), 2 (split-bf16), 3 (three-part split); 0: FP8 E4M3
     bool zreg, lean;
 };
 
@@ -1165,12 +1347,15 @@ bool with_kernel(const Variant& v, F&& f) {
         TC_VAR4(NN, WW, 2, false)       \
         TC_VAR4(NN, WW, 1, true)        \
         TC_VAR4(NN, WW, 1, false)       \
+        TC_VAR4(NN, WW, 0, true)        \
+        TC_VAR4(NN, WW, 0, false)       \
     }
-// two warpgroups: 1 or 2 parts, z in TMEM
+// two warpgroups: FP8, 1 or 2 parts, z in TMEM
 #define TC_VARIANT_NOZ(NN, WW)          \
     if (v.N == NN && v.nwg == WW) {     \
         TC_VAR4(NN, WW, 2, false)       \
         TC_VAR4(NN, WW, 1, false)       \
+        TC_VAR4(NN, WW, 0, false)       \
     }
     TC_VARIANT(16, 1)
     TC_VARIANT(32, 1)
@@ -1217,14 +1402,16 @@ TcSmem smem_layout(int N, int dp, int de, int d, int n_cls, int n_d, int n_slots
 
 }  // namespace
 
-// bf16 parts per operand of a tensor-core precision (0: not offered).
+// bf16 parts per operand of a tensor-core precision, 0 for FP8 E4M3 (-1:
+// not a tensor-core precision).
 int precision_parts(int precision) {
     switch (precision) {
         case TABNET_BF16: return 1;
         case TABNET_BF16X3: return 2;
         case TABNET_BF16X6: return 3;
+        case TABNET_FP8_E4M3: return 0;
     }
-    return 0;
+    return -1;
 }
 
 int tc_build(tabnet_model* m, Arena& a, std::string* why) {
@@ -1232,9 +1419,9 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
     const int N = d.n_d + d.n_a;
     const int dp = round_up(d.d_emb, 16);
     const int np = precision_parts(m->precision);
-    const bool split = np > 1;
-    if (np == 0) {
-        *why = "FP8 E4M3 is not offered: E4M3 operands move the sparsemax masks of most rows";
+    const bool fp8 = np == 0;
+    if (np < 0) {
+        *why = "not a tensor-core precision";
         return TABNET_ERR_UNSUPPORTED_DIMS;
     }
     if (N != 16 && N != 32 && N != 64 && N != 128) {
@@ -1270,7 +1457,11 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
     p.m16 = m16 ? 1 : 0;
     p.tm_p = accw;
     p.tm_m = accw + pw;
-    p.att_k0 = d.n_d / 16;
+    // K steps: 16 bf16 or 32 e4m3 elements
+    const int kstep = fp8 ? 32 : 16;
+    p.att_k0 = d.n_d / kstep;
+    p.ks_0 = (dp + kstep - 1) / kstep;
+    p.ks_n = (N + kstep - 1) / kstep;
     // the aggregate lives in TMEM when every feature is one embedded column
     // and its region fits in the allocation (or the next, <= 256)
     p.tm_agg = -1;
@@ -1281,7 +1472,8 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
     p.tmem_cols = cols;
 
     const HostModel& hm = m->host;
-    const int parts = np;
+    const int parts = fp8 ? 1 : np;
+    const int kblock = fp8 ? 128 : 64;  // elements of a K block (128 bytes a row)
     // Every 64-wide K block of W (its parts in order: hi, then lo or mid, lo) becomes a chunk.
     // Blocks before first_block are not streamed (all their weights are 0).
     auto push_layer = [&](const float* W, int n_out, int k_valid, int col_shift, int k_pad, int first_block,
@@ -1296,6 +1488,31 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
                 keep->push_back({off, cb});
             }
     };
+    // FP8: W' = diag(BN scale) W in double (as the rounding study folds it),
+    // quantized per output channel; the kernel's per-channel scale also
+    // carries the row's constant pre-scale c (sqrt(1/2) or -log2 e), which
+    // leaves the quantized bytes unchanged.
+    std::vector<float> wsc;  // per-channel dequantization scales, laid out like epi
+    auto push_layer_e4m3 = [&](const std::vector<float>& W, const BN& bn, int n_out, int k_valid, int col_shift,
+                               int k_pad, int first_block, const std::vector<double>& c,
+                               std::vector<std::pair<size_t, uint32_t>>* keep, std::vector<float>* scales) {
+        std::vector<double> wd((size_t)n_out * k_valid, 0.0);
+        const int n_bn = (int)bn.mean.size();
+        for (int r = 0; r < n_out && r < n_bn; ++r) {
+            const double sbn = (double)bn.weight[r] / std::sqrt((double)bn.var[r] + d.bn_eps);
+            for (int k = 0; k < k_valid; ++k) wd[(size_t)r * k_valid + k] = sbn * (double)W[(size_t)r * k_valid + k];
+        }
+        std::vector<uint8_t> pk;
+        std::vector<double> sc;
+        pack_e4m3(wd.data(), n_out, k_valid, col_shift, k_pad, pk, sc);
+        for (int r = 0; r < n_out; ++r) scales->push_back((float)(sc[r] * (r < (int)c.size() ? c[r] : 1.0)));
+        const uint32_t cb = (uint32_t)n_out * 128;
+        const int blocks = (k_pad + 127) / 128;
+        for (int b = first_block; b < blocks; ++b) {
+            const size_t off = a.add(pk.data() + (size_t)b * cb, cb, 1024);
+            keep->push_back({off, cb});
+        }
+    };
     // BN scale is folded into the packed weights (W' = diag(scale) W, rounded
     // after scaling, so a shared layer gets one packed copy per feature
     // transformer); the epilogue adds the BN shift only.
@@ -1306,7 +1523,7 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
         return w;
     };
     std::vector<std::pair<size_t, uint32_t>> stream;
-    std::vector<float> epi, att_epi;
+    std::vector<float> epi, att_epi, att_wsc;
     for (int s = 0; s <= d.n_steps; ++s) {
         if (s > 0) {
             // attentive FC [de, n_a] acting on the whole FT output [N] as
@@ -1314,12 +1531,18 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
             // de (padding) carry zero weight
             std::vector<float> sc, sh;
             fold_bn(hm.att_bn[s - 1], d.bn_eps, sc, sh);
-            std::vector<float> wp((size_t)dp * d.n_a, 0.f);
-            const std::vector<float> ws = scaled(hm.att_fc[s - 1], sc, d.d_emb, d.n_a);
-            std::memcpy(wp.data(), ws.data(), sizeof(float) * d.d_emb * d.n_a);
-            // the MMA chain starts at K step n_d / 16: blocks wholly inside the
+            // the MMA chain starts at K step att_k0: blocks wholly inside the
             // decision half are not streamed
-            push_layer(wp.data(), dp, d.n_a, d.n_d, N, (d.n_d / 16) / 4, &stream);
+            if (fp8) {
+                std::vector<float> wraw((size_t)dp * d.n_a, 0.f);
+                std::memcpy(wraw.data(), hm.att_fc[s - 1].data(), sizeof(float) * d.d_emb * d.n_a);
+                push_layer_e4m3(wraw, hm.att_bn[s - 1], dp, d.n_a, d.n_d, N, p.att_k0 / 4, {}, &stream, &att_wsc);
+            } else {
+                std::vector<float> wp((size_t)dp * d.n_a, 0.f);
+                const std::vector<float> ws = scaled(hm.att_fc[s - 1], sc, d.d_emb, d.n_a);
+                std::memcpy(wp.data(), ws.data(), sizeof(float) * d.d_emb * d.n_a);
+                push_layer(wp.data(), dp, d.n_a, d.n_d, N, p.att_k0 / 4, &stream);
+            }
             sh.resize(dp, 0.f);
             att_epi.insert(att_epi.end(), sh.begin(), sh.end());
         }
@@ -1327,27 +1550,43 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
             GluLayer g = hm.layer(s, l);
             std::vector<float> sc, sh;
             fold_bn(*g.bn, d.bn_eps, sc, sh);
-            if (l > 0) {
-                // linear half pre-scaled by sqrt(1/2): the kernel forms the
-                // residual sqrt(1/2) (x + g) as x sqrt(1/2) + g
-                for (int n = 0; n < N; ++n) {
-                    sc[n] = (float)((double)sc[n] * 0.70710678118654752440);
-                    sh[n] = (float)((double)sh[n] * 0.70710678118654752440);
-                }
+            // The kernel scales the linear half of every layer but an FT's
+            // first by sqrt(1/2) (it forms the residual sqrt(1/2) (x + g) as
+            // x sqrt(1/2) + g) and the gate half by -log2(e) (its sigmoid takes
+            // 2^(-x log2 e)): the shifts are stored pre-scaled.  With several
+            // bf16 parts the weights are pre-scaled too; with one part (bf16,
+            // FP8) they are packed unscaled, BN-folded and then rounded, so the
+            // rounding is that of the BN-folded weight, and the kernel applies
+            // the constant to the accumulator.
+            const bool prescale_w = np >= 2;
+            for (int n = 0; n < N && l > 0; ++n) {
+                sh[n] = (float)((double)sh[n] * 0.70710678118654752440);
+                if (prescale_w) sc[n] = (float)((double)sc[n] * 0.70710678118654752440);
             }
-            if (split) {
-                // gate half pre-scaled by -log2(e): the kernel's sigmoid takes 2^(-x log2 e) directly
-                for (int n = N; n < 2 * N; ++n) {
-                    sc[n] = (float)((double)sc[n] * -1.4426950408889634);
-                    sh[n] = (float)((double)sh[n] * -1.4426950408889634);
-                }
+            for (int n = N; n < 2 * N; ++n) {
+                sh[n] = (float)((double)sh[n] * -1.4426950408889634);
+                if (prescale_w) sc[n] = (float)((double)sc[n] * -1.4426950408889634);
             }
-            const std::vector<float> ws = scaled(*g.w, sc, 2 * N, g.k);
-            push_layer(ws.data(), 2 * N, g.k, 0, l == 0 ? dp : N, 0, &stream);
+            if (fp8) {
+                std::vector<double> c(2 * N, 1.0);
+                for (int n = 0; n < N; ++n) c[n] = l > 0 ? 0.70710678118654752440 : 1.0;
+                for (int n = N; n < 2 * N; ++n) c[n] = -1.4426950408889634;
+                push_layer_e4m3(*g.w, *g.bn, 2 * N, g.k, 0, l == 0 ? dp : N, 0, c, &stream, &wsc);
+            } else {
+                const std::vector<float> ws = scaled(*g.w, sc, 2 * N, g.k);
+                push_layer(ws.data(), 2 * N, g.k, 0, l == 0 ? dp : N, 0, &stream);
+            }
             epi.insert(epi.end(), sh.begin(), sh.end());
         }
     }
     epi.insert(epi.end(), att_epi.begin(), att_epi.end());
+    p.epi_sc = 0;
+    if (fp8) {
+        // the per-channel weight scales follow the shifts, in the same layout
+        wsc.insert(wsc.end(), att_wsc.begin(), att_wsc.end());
+        p.epi_sc = (int)epi.size();
+        epi.insert(epi.end(), wsc.begin(), wsc.end());
+    }
     m->tc_chunk_off.clear();
     m->tc_chunk_bytes.clear();
     for (auto& c : stream) {
@@ -1401,7 +1640,7 @@ int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std
     const int reg_limit = 65536 / (((regs * 32 + 255) / 256 * 256) * (threads / 32));
     const int tmem_limit = 512 / p.tmem_cols;
     const int slot_bytes = std::max(2 * N, p.dp) * 128;
-    const int min_slots = np;  // one K block's parts
+    const int min_slots = std::max(np, 1);  // one K block's parts
     int cps_max = std::max(1, std::min({tmem_limit, reg_limit, 4}));
     int best_cps = 0, best_slots = 0;
     bool best_epi = false, best_f = false, best_mst = false;

@@ -41,8 +41,13 @@ struct TcParams {
     const int2* col_info;      // [dp]: {-1, numeric column} | {categorical j, element e} | {-2, 0} pad
     const int* col_feat;       // [dp]: original feature of each embedded column (-1 for pad)
     int dp;                    // mask width padded to a multiple of 16
-    int att_k0;                // first K step (16 columns) of the attentive layer: n_d / 16, the
-                               // decision half's weights before it being zero
+    int att_k0;                // first K step of the attentive layer (n_d / K step; the decision
+                               // half's weights before it are zero)
+    int ks_0;                  // K steps of a feature transformer's first layer (K = dp)
+    int ks_n;                  // K steps of the other layers (K = N); a K step is 16 bf16 or
+                               // 32 e4m3 elements
+    int epi_sc;                // FP8: float offset in epi of the per-output-channel weight
+                               // scales (laid out like the shifts); 0 otherwise
     int tmem_cols;             // TMEM columns allocated per CTA
     // P, the step mask and the aggregate are fp32 regions of dp columns, or
     // dp - 8 when the last 16-column chunk holds at most 8 mask columns (tail8)

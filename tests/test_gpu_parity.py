@@ -245,15 +245,6 @@ def test_host_buffer_entry_point(tabnet_mod):
         np.testing.assert_array_equal(a, b)
 
 
-def test_fp8_is_refused(tabnet_mod):
-    """No E4M3 path is built (the rounding study shows E4M3 operands move the
-    masks of most rows): creating an FP8 model fails with UNSUPPORTED_DIMS."""
-    params = synth.make_params(synth.SPECS["c1"], 3)
-    with pytest.raises(tabnet_mod.TabnetError) as e:
-        tabnet_mod.Model(synth.to_blob(params), "fp8")
-    assert e.value.code == -6 and "E4M3" in str(e.value)
-
-
 def test_outputs_past_the_int32_element_range(tabnet_mod):
     """1,400,000 rows of the 100-input model in one launch: the step masks
     hold 2.24e9 elements, past 2^31, so every row-offset product must be

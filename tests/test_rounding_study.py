@@ -2,10 +2,10 @@
 
 The split-bf16 mode exists because rounding every tensor-core operand once to
 bf16 moves the sparsemax masks past the stated bf16 bar, while hi + lo
-pairs keep them inside it; no FP8 path exists because E4M3 operands move the
-masks of most rows (mean per-row mask L1 far above the 5e-2 a usable FP8
-mode would need).  These tests pin the study's rounding functions to
-independent definitions and re-derive those claims on seeded rows.
+pairs keep them inside it; E4M3 operands move the masks of most rows (mean
+per-row mask L1 far above 5e-2), which is the FP8 mode's stated error.  These
+tests pin the study's rounding functions to independent definitions and
+re-derive those claims on seeded rows.
 """
 import numpy as np
 import pytest
