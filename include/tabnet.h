@@ -201,11 +201,9 @@ int tabnet_reserve_segments(tabnet_model* model, int max_segs);
 /* tabnet_forward_segments_device for callers that cannot allocate device
  * memory.  (The paper has no counterpart: this is a deployment convenience of
  * this library.)  Some callers must not call cudaMalloc once they are
- * running: code that launches while a CUDA graph is being captured in the
- * default (global) capture mode, where allocation calls are refused; serving
- * processes that fix their device memory at start-up so that no request can
- * fail or stall on an allocation; hosts that give a plug-in only memory they
- * allocated themselves.  This entry point allocates nothing: the prefix sums
+ * running: serving processes that fix their device memory at start-up so
+ * that no request can fail or stall on an allocation, and hosts that give a
+ * plug-in only memory they allocated themselves.  This entry point allocates nothing: the prefix sums
  * of the segments' row counts (its only scratch) live in a fixed array in the
  * library's device image, TABNET_NOALLOC_MAX_SEGMENTS + 1 entries (512 KB),
  * held by every GPU that loads the library until the process exits.
