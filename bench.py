@@ -113,28 +113,85 @@ def profiled_traffic(workload, precision):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    """SM clock, power and throttle reasons sampled while running: through
+    NVML every `period_s` (1 ms by default, so that even a few-millisecond
+    timed region is sampled), else through nvidia-smi every 200 ms."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+               ("sw_power_cap", 0x4))
 
-    def __init__(self, index):
-        self.index = index
+    def __init__(self, device, period_s=0.001):
+        self.device = device
+        self.period_s = period_s
+        self.samples = []  # (sm_mhz, max_sm_mhz, power_w, reason bits)
         self.proc = None
+        self.thread = None
+        self.how = None
+
+    @staticmethod
+    def _nvml():
+        """The driver's NVML library through ctypes (documented C API)."""
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        return lib
+
+    def _nvml_handle(self, lib):
+        import ctypes
+        import torch
+        h = ctypes.c_void_p()
+        props = torch.cuda.get_device_properties(self.device)
+        bus = getattr(props, "pci_bus_id", None)
+        if bus is not None:
+            pci = f"{getattr(props, 'pci_domain_id', 0):08x}:{bus:02x}:{getattr(props, 'pci_device_id', 0):02x}.0"
+            if lib.nvmlDeviceGetHandleByPciBusId_v2(pci.encode(), ctypes.byref(h)) == 0:
+                return h
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.device), ctypes.byref(h)) != 0:
+            raise OSError("no NVML handle")
+        return h
 
     def __enter__(self):
+        import ctypes
+        import threading
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.proc = None
+            lib = self._nvml()
+            h = self._nvml_handle(lib)
+            mx, sm, pw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) != 0:  # 1 = NVML_CLOCK_SM
+                raise OSError("NVML max clock")
+            reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.stop = threading.Event()
+
+            def run():
+                while not self.stop.is_set():
+                    if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(sm)) == 0
+                            and lib.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw)) == 0
+                            and reasons(h, ctypes.byref(rs)) == 0):
+                        self.samples.append((float(sm.value), float(mx.value), pw.value / 1000.0, int(rs.value)))
+                    self.stop.wait(self.period_s)
+
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            self.how = f"NVML every {self.period_s * 1e3:g} ms"
+        except Exception:
+            self.thread = None
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.device),
+                     "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active",
+                     "--format=csv,noheader,nounits", "-lms", "200"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.how = "nvidia-smi every 200 ms"
+            except OSError:
+                self.proc = None
         return self
 
     def __exit__(self, *a):
-        self.lines = []
+        if self.thread is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
         if self.proc:
             self.proc.terminate()
             try:
@@ -142,27 +199,21 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
                 out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            for l in out.splitlines():
+                f = [x.strip() for x in l.split(",")]
+                try:
+                    self.samples.append((float(f[0]), float(f[1]), float(f[2]), int(f[3], 16)))
+                except (ValueError, IndexError):
+                    continue
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
-            f = [x.strip() for x in l.split(",")]
-            if len(f) < 8:
-                continue
-            try:
-                sm.append(float(f[0]))
-                mx.append(float(f[1]))
-            except ValueError:
-                continue
-            for n, v in zip(names, f[4:8]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "how": self.how}
+        sm = [x[0] for x in self.samples]
+        reasons = sorted({n for *_, bits in self.samples for n, b in self.REASONS if bits & b})
+        return {"sm_mhz": statistics.median(sm), "sm_min_mhz": min(sm), "sm_max_mhz": max(x[1] for x in self.samples),
+                "power_w_max": max(x[2] for x in self.samples), "reasons": reasons, "samples": len(sm),
+                "how": self.how}
 
 
 def oracle_rows_per_s(params, x_num, x_cat):
@@ -204,11 +255,12 @@ def run_reference(args):
     ms = 1e3 * sum(ts) / len(ts)
     value = sample_rows / (ms / 1e3)
     sample = f"{sample_rows} rows of the {name} workload per step (float64 numpy oracle)"
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": describe(name), "sample_rows": sample_rows},
+        "config": workload_config(name, args.precision, world), "sample_rows_per_step": sample_rows,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -327,14 +379,231 @@ def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), s
             "rates": out}
 
 
+def spec_params(name):
+    """The shape fields of workload ``name`` (what the MAC and byte counts read)."""
+    from paper_2510_19689_b300 import synth
+    sp = synth.SPECS[name]
+    return dict(n_num=sp.n_num, cat_card=list(sp.cat_card), cat_emb_dim=list(sp.cat_emb_dim), n_d=sp.n_d,
+                n_a=sp.n_a, n_steps=sp.n_steps, n_classes=sp.n_classes, n_shared=sp.n_shared, n_indep=sp.n_indep)
+
+
+def n_sets_for(name):
+    """Rotating input/output sets so that consecutive steps never find their
+    buffers in L2 (at least twice L2 in all)."""
+    from paper_2510_19689_b300 import synth
+    inp_b, out_b = bytes_per_row(spec_params(name))
+    set_bytes = synth.ROWS[name] * (inp_b + out_b)
+    return max(2, math.ceil(2 * L2_BYTES / set_bytes)), set_bytes
+
+
+def workload_config(name, precision, world):
+    """The `config` object of the JSON line -- the same in both arms."""
+    from paper_2510_19689_b300 import synth
+    n_sets, set_bytes = n_sets_for(name)
+    return {"workload": describe(name), "rows_per_gpu": synth.ROWS[name], "precision": precision,
+            "parallelism": f"replicas x{world} (rows sharded per GPU, no collective)",
+            "l2": f"{n_sets} rotating input/output sets of {set_bytes / 1e6:.1f} MB "
+                  f"({n_sets * set_bytes / 1e6:.0f} MB > L2)"}
+
+
+class Workload:
+    """One workload resident on the device: its model at one precision and
+    `n_sets` rotating input/output sets."""
+
+    def __init__(self, name, precision, dev, data=None):
+        import torch
+        from paper_2510_19689_b300 import synth, tabnet
+        self.name, self.precision, self.dev = name, precision, dev
+        self.params, self.blob, self.x_num, self.x_cat = data if data is not None else synth.load_config(name)
+        self.rows = self.x_num.shape[0]
+        self.model = tabnet.Model(self.blob, precision, device=dev.index)
+        d = self.model.dims
+        self.n_sets, _ = n_sets_for(name)
+        xn = torch.from_numpy(self.x_num).to(dev)
+        xc = torch.from_numpy(self.x_cat).to(dev)
+        self.sets = [dict(xn=xn if k == 0 else xn.clone(), xc=xc if k == 0 else xc.clone(),
+                          lg=torch.empty((self.rows, d.n_classes), device=dev),
+                          mk=torch.empty((self.rows, d.n_steps, d.d_emb), device=dev),
+                          ag=torch.empty((self.rows, d.n_feat), device=dev)) for k in range(self.n_sets)]
+        self.stream = torch.cuda.current_stream(dev)
+        self.tile = None
+
+    def step(self, k):
+        s = self.sets[k % self.n_sets]
+        self.model.forward(s["xn"], s["xc"], self.rows, s["lg"], s["mk"], s["ag"], stream=self.stream)
+
+    def tune(self, enabled=True):
+        from paper_2510_19689_b300 import autotune
+        if self.precision != "fp32":
+            if enabled:
+                s0 = self.sets[0]
+                autotune.tune(self.model, s0["xn"], s0["xc"], self.rows, s0["lg"], s0["mk"], s0["ag"],
+                              stream=self.stream, cache_path=None)
+            self.tile = self.model.tile_config()
+
+    def time(self, steps, warmup, group=None):
+        """Exactly `steps` steps between synchronised events (max over ranks);
+        clocks sampled in the region."""
+        import numpy as np
+        import torch
+        for k in range(warmup):
+            self.step(k)
+        torch.cuda.synchronize()
+        if group:
+            group.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        with ClockSampler(self.dev.index) as clk:
+            torch.cuda.synchronize()
+            e0.record(self.stream)
+            for k in range(steps):
+                self.step(k)
+                marks[k].record(self.stream)
+            e1.record(self.stream)
+            e1.synchronize()
+        if group:
+            group.barrier()
+        per = [e0.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k]) for k in range(1, steps)]
+        ms_total = group.max(e0.elapsed_time(e1)) if group else e0.elapsed_time(e1)
+        return ms_total, {"min": float(np.min(per)), "median": float(np.median(per)), "max": float(np.max(per))}, \
+            clk.summary()
+
+    def sustained(self, seconds=1.0, batch=50):
+        """Steps back to back for at least `seconds` of device time, clocks
+        sampled throughout: the rate under the power cap."""
+        import torch
+        done, ms = 0, 0.0
+        with ClockSampler(self.dev.index, period_s=0.005) as clk:
+            while ms < 1e3 * seconds:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(self.stream)
+                for k in range(batch):
+                    self.step(done + k)
+                e1.record(self.stream)
+                e1.synchronize()
+                ms += e0.elapsed_time(e1)
+                done += batch
+        return {"value": self.rows * done / (ms / 1e3), "unit": UNIT, "steps": done, "seconds": ms / 1e3,
+                "ms_per_step": ms / done, "clocks": clk.summary()}
+
+    def e2e(self, steps=20):
+        """The same metric through the host-buffer entry point (pinned host
+        memory, both copies inside the timed region)."""
+        import torch
+        from paper_2510_19689_b300 import tabnet
+        d = self.model.dims
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+        xn_p, xc_p = pin(self.x_num), pin(self.x_cat)
+        lg_p = torch.empty((self.rows, d.n_classes)).pin_memory().numpy()
+        mk_p = torch.empty((self.rows, d.n_steps, d.d_emb)).pin_memory().numpy()
+        ag_p = torch.empty((self.rows, d.n_feat)).pin_memory().numpy()
+        args = [tabnet._ptr(xn_p), tabnet._ptr(xc_p), self.rows, tabnet._ptr(lg_p), tabnet._ptr(mk_p),
+                tabnet._ptr(ag_p), self.stream.cuda_stream]
+        L = tabnet.lib()
+        for _ in range(3):
+            tabnet._check(L.tabnet_forward_host(self.model._h, *args), "tabnet_forward_host")
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            tabnet._check(L.tabnet_forward_host(self.model._h, *args), "tabnet_forward_host")
+        sec = (time.perf_counter() - t0) / steps
+        inp_b, out_b = bytes_per_row(self.params)
+        return {"value": self.rows / sec, "unit": UNIT, "h2d_bytes_per_step": self.rows * inp_b,
+                "d2h_bytes_per_step": self.rows * out_b}
+
+    def parity(self, n=256):
+        """256 rows spread over the batch against the FP64 oracle (and, for the
+        single-rounding modes, the error the rounding itself causes)."""
+        import numpy as np
+        import torch
+        from oracle import tabnet_oracle as O
+        self.step(0)
+        torch.cuda.synchronize()
+        status = self.model.poll_status()
+        idx = np.linspace(0, self.rows - 1, n).astype(np.int64)
+        rl, rm, ra = O.forward(self.params, self.x_num[idx], self.x_cat[idx])
+        it = torch.from_numpy(idx).to(self.dev)
+        s0 = self.sets[0]
+        lg, mk, ag = s0["lg"][it].cpu().numpy(), s0["mk"][it].cpu().numpy(), s0["ag"][it].cpu().numpy()
+        l1 = np.abs(mk - rm).sum((1, 2))
+        return {"sample_rows": n, "logit_abs_max": float(np.abs(lg - rl).max()),
+                "logit_rel_max": float((np.abs(lg - rl) / np.maximum(np.abs(rl), 1)).max()),
+                "mask_l1_max": float(l1.max()), "mask_l1_mean": float(l1.mean()),
+                "agg_l1_max": float(np.abs(ag - ra).sum(1).max()),
+                "argmax_agreement": float((lg.argmax(1) == rl.argmax(1)).mean()), "status": status}
+
+    def cpu_baseline(self, seconds=10.0):
+        """The FP64 oracle as it stands on the host cores: a bounded sample of
+        about `seconds` of CPU work (the batch's first rows, repeated when the
+        batch takes less)."""
+        from oracle import tabnet_oracle as O
+        n_probe = {"c1": 256, "c2": 1024, "c3": 128}[self.name]
+        rp, cores, _ = oracle_rows_per_s(self.params, self.x_num[:n_probe], self.x_cat[:n_probe])
+        n_cpu = int(min(self.rows, max(n_probe, rp * seconds)))
+        _, _, t_one = oracle_rows_per_s(self.params, self.x_num[:n_cpu], self.x_cat[:n_cpu])
+        reps = max(1, int(round(seconds / t_one)))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            O.forward(self.params, self.x_num[:n_cpu], self.x_cat[:n_cpu])
+        dt = time.perf_counter() - t0
+        return {"value": n_cpu * reps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"first {n_cpu} rows of the {self.name} batch x {reps} passes, float64 numpy ({dt:.1f} s)"}
+
+    def close(self):
+        self.model.close()
+        self.sets = []
+
+
+def roofline_for(params, rows, ms_step, precision, sustained, fp8_peak=None, traffic=None):
+    """Algorithmic FLOP per launch over the event-timed launch duration,
+    against the measured peak of the operands' type (bf16 for every bf16
+    mode -- the split modes' extra products are not algorithmic work -- and
+    the measured E4M3 GEMM rate for FP8)."""
+    pk = peaks()
+    flop = 2.0 * mac_per_row(params) * rows
+    achieved = flop / (ms_step / 1e3) / 1e12
+    if precision == "fp8" and fp8_peak:
+        peak = fp8_peak * (pk["bf16_sus"] / pk["bf16"] if sustained else 1.0)
+        kind = ("fp8 e4m3 GEMM measured in this run" + (" x the bf16 sustained/burst ratio" if sustained else "")
+                + f" (bf16 peaks of {pk['src']})")
+    else:
+        peak = pk["bf16_sus"] if sustained else pk["bf16"]
+        kind = ("bf16 sustained" if sustained else "bf16 burst") + f", of {pk['src']}"
+    inp_b, out_b = bytes_per_row(params)
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": kind, "flop_per_launch": flop,
+            "hbm_frac": rows * (inp_b + out_b) / (ms_step / 1e3) / 1e9 / pk["hbm"]}
+
+
+def other_precisions(w, prec_list, steps, extras, it_rows=256):
+    """The other precisions of the fused library on the same batch: rate and
+    parity on the same sampled rows."""
+    import torch
+    from paper_2510_19689_b300 import tabnet
+    for prec in prec_list:
+        if prec == w.precision:
+            continue
+        try:
+            w2 = Workload(w.name, prec, w.dev, data=(w.params, w.blob, w.x_num, w.x_cat))
+        except tabnet.TabnetError as exc:
+            extras[f"fused_{prec}"] = {"value": None, "unavailable": str(exc)[:200]}
+            continue
+        w2.tune()
+        ms, stats, clocks = w2.time(steps if prec != "fp32" else 3, 2)
+        n = steps if prec != "fp32" else 3
+        extras[f"fused_{prec}"] = {"value": w2.rows * n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / n,
+                                   "tile": w2.tile, "parity": w2.parity(it_rows)}
+        w2.close()
+        del w2
+        torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
         return
-    import numpy as np
     import torch
-    from paper_2510_19689_b300 import autotune, replicas, synth, tabnet
+    from paper_2510_19689_b300 import replicas
 
     # one process per GPU; rows are independent, so each rank runs its own
     # replica on its own batch (weak scaling, no collective in the step)
@@ -343,213 +612,83 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     name = args.workload
-    params, blob, x_num_h, x_cat_h = synth.load_config(name)
-    rows = x_num_h.shape[0]
-    model = tabnet.Model(blob, args.precision, device=local)
-    d = model.dims
-    inp_b, out_b = bytes_per_row(params)
-    set_bytes = rows * (inp_b + out_b)
-    n_sets = max(2, math.ceil(2 * L2_BYTES / set_bytes))
-    sets = []
-    for _ in range(n_sets):
-        sets.append(dict(
-            xn=torch.from_numpy(x_num_h).to(dev), xc=torch.from_numpy(x_cat_h).to(dev),
-            lg=torch.empty((rows, d.n_classes), device=dev),
-            mk=torch.empty((rows, d.n_steps, d.d_emb), device=dev),
-            ag=torch.empty((rows, d.n_feat), device=dev)))
-    stream = torch.cuda.current_stream(dev)
+    w = Workload(name, args.precision, dev)
+    w.tune(not args.no_tune)
+    parity = w.parity()
 
-    def step(k):
-        s = sets[k % n_sets]
-        model.forward(s["xn"], s["xc"], rows, s["lg"], s["mk"], s["ag"], stream=stream)
-
-    tile = None
-    if args.precision != "fp32":
-        s0 = sets[0]
-        if not args.no_tune:
-            autotune.tune(model, s0["xn"], s0["xc"], rows, s0["lg"], s0["mk"], s0["ag"], stream=stream,
-                          cache_path=None)
-        tile = model.tile_config()
-
-    # parity on a sample against the FP64 oracle (bench inputs, bench launch shape)
-    step(0)
-    torch.cuda.synchronize()
-    status = model.poll_status()
-    from oracle import tabnet_oracle as O
-    idx = np.linspace(0, rows - 1, 256).astype(np.int64)
-    rl, rm, ra = O.forward(params, x_num_h[idx], x_cat_h[idx])
-    it = torch.from_numpy(idx).to(dev)
-    lg = sets[0]["lg"][it].cpu().numpy()
-    mk = sets[0]["mk"][it].cpu().numpy()
-    ag = sets[0]["ag"][it].cpu().numpy()
-    parity = {"sample_rows": len(idx), "logit_abs_max": float(np.abs(lg - rl).max()),
-              "mask_l1_max": float(np.abs(mk - rm).sum((1, 2)).max()),
-              "agg_l1_max": float(np.abs(ag - ra).sum(1).max()),
-              "argmax_agreement": float((lg.argmax(1) == rl.argmax(1)).mean()), "status": status}
-
-    for k in range(args.warmup):
-        step(k)
-    torch.cuda.synchronize()
-    group.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    # an event after every step (recorded on the stream, no synchronisation)
-    # gives the per-step spread; the total is e0 -> e1 as always
-    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for k in range(args.steps):
-            step(k)
-            marks[k].record(stream)
-        e1.record(stream)
-        e1.synchronize()
-    group.barrier()
-    per_step = [e0.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k]) for k in range(1, args.steps)]
-    step_stats = {"min": float(np.min(per_step)), "median": float(np.median(per_step)),
-                  "max": float(np.max(per_step))}
-    ms_total = group.max(e0.elapsed_time(e1))
+    ms_total, step_stats, clocks = w.time(args.steps, args.warmup, group)
     ms_step = ms_total / args.steps
-    value = replicas.throughput(group.sum(rows * args.steps), ms_total)
-    clocks = clk.summary()
+    value = replicas.throughput(group.sum(w.rows * args.steps), ms_total)
+    traffic = profiled_traffic(name, args.precision) if args.precision != "fp32" else None
 
     extras = {}
+    fp8_peak = None
+    if rank == 0 and not args.no_extras and (args.precision == "fp8" or name == "c2"):
+        extras["fp8_gemm_peak"] = fp8_gemm_peak(dev)
+        fp8_peak = extras["fp8_gemm_peak"].get("value")
+    roofline = roofline_for(w.params, w.rows, ms_step, args.precision, False, fp8_peak, traffic)
     if rank == 0:
-        # end to end through the host-buffer entry point (pinned host memory)
-        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
-        xn_p, xc_p = pin(x_num_h), pin(x_cat_h)
-        lg_p = torch.empty((rows, d.n_classes)).pin_memory().numpy()
-        mk_p = torch.empty((rows, d.n_steps, d.d_emb)).pin_memory().numpy()
-        ag_p = torch.empty((rows, d.n_feat)).pin_memory().numpy()
-        host_args = [tabnet._ptr(xn_p), tabnet._ptr(xc_p), rows, tabnet._ptr(lg_p), tabnet._ptr(mk_p),
-                     tabnet._ptr(ag_p), stream.cuda_stream]
-        L = tabnet.lib()
-        for _ in range(3):
-            tabnet._check(L.tabnet_forward_host(model._h, *host_args), "tabnet_forward_host")
-        e2e_steps = 20
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            tabnet._check(L.tabnet_forward_host(model._h, *host_args), "tabnet_forward_host")
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
-        extras["e2e"] = {"value": rows / e2e_s, "unit": UNIT, "h2d_bytes_per_step": rows * inp_b,
-                         "d2h_bytes_per_step": rows * out_b}
-
-    pk = peaks()
-    flop_launch = 2.0 * mac_per_row(params) * rows
-    achieved = flop_launch / (ms_step / 1e3) / 1e12
-    sustained = ms_total > 1000.0
-    peak = pk["bf16_sus"] if sustained else pk["bf16"]
-    traffic = profiled_traffic(name, args.precision) if args.precision != "fp32" else None
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "peak_kind": ("bf16 sustained" if sustained else "bf16 burst") + f", of {pk['src']}",
-                "flop_per_launch": flop_launch,
-                "hbm_frac": (rows * (inp_b + out_b)) / (ms_step / 1e3) / 1e9 / pk["hbm"]}
+        extras["e2e"] = w.e2e()
+        # the same step back to back for >= 1 s under the power cap
+        sus = w.sustained(1.0)
+        sus["roofline"] = roofline_for(w.params, w.rows, sus["ms_per_step"], args.precision, True, fp8_peak, traffic)
+        extras["sustained"] = sus
 
     if rank == 0 and not args.no_extras:
-        # the FP64 oracle on the host cores: a bounded sample of about 10 s of
-        # CPU work (the batch's first rows, the whole batch repeated when it
-        # takes less), sized from a short probe
-        from oracle import tabnet_oracle as O
-        n_probe = {"c1": 256, "c2": 1024, "c3": 128}[name]
-        rp, cores, _ = oracle_rows_per_s(params, x_num_h[:n_probe], x_cat_h[:n_probe])
-        n_cpu = int(min(rows, max(n_probe, rp * 10.0)))
-        _, _, t_one = oracle_rows_per_s(params, x_num_h[:n_cpu], x_cat_h[:n_cpu])  # one pass at full size
-        reps = max(1, int(round(10.0 / t_one)))
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            O.forward(params, x_num_h[:n_cpu], x_cat_h[:n_cpu])
-        dt = time.perf_counter() - t0
-        extras["cpu_baseline"] = {"value": n_cpu * reps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                  "sample": f"first {n_cpu} rows of the {name} batch x {reps} passes, "
-                                            f"float64 numpy ({dt:.1f} s)"}
+        extras["cpu_baseline"] = w.cpu_baseline()
         # the same oracle held to one host thread (a child process whose BLAS
         # pools are limited by the environment before numpy loads), about 5 s
         env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        n_probe = {"c1": 256, "c2": 1024, "c3": 128}[name]
         code = ("import sys, time, json; sys.path.insert(0, %r); from paper_2510_19689_b300 import synth; "
-                "from oracle import tabnet_oracle as O; p, _, xn, xc = synth.load_config(%r); "
+                "from oracle import tabnet_oracle as O; p, _, xn, xc = synth.load_config(%r, rows=%d); "
                 "t = time.perf_counter(); O.forward(p, xn[:%d], xc[:%d]); r = %d / (time.perf_counter() - t); "
                 "n = int(min(len(xn), max(%d, r * 5.0))); "
                 "t = time.perf_counter(); O.forward(p, xn[:n], xc[:n]); k = max(1, int(round(5.0 / (time.perf_counter() - t)))); "
                 "t = time.perf_counter(); [O.forward(p, xn[:n], xc[:n]) for _ in range(k)]; "
                 "dt = time.perf_counter() - t; print(json.dumps([n * k / dt, n, k, dt]))"
-                ) % (ROOT, name, n_probe, n_probe, n_probe, n_probe)
+                ) % (ROOT, name, min(w.rows, 65536), n_probe, n_probe, n_probe, n_probe)
         try:
             out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
             r1, n1, k1, dt1 = json.loads(out.stdout.strip().splitlines()[-1])
-            extras["cpu_baseline"]["one_core"] = {"value": r1,
-                                                  "sample": f"first {n1} rows x {k1} passes ({dt1:.1f} s)"}
+            extras["cpu_baseline"]["one_core"] = {"value": r1, "sample": f"first {n1} rows x {k1} passes ({dt1:.1f} s)"}
         except Exception as exc:
             extras["cpu_baseline"]["one_core"] = {"value": None, "unavailable": str(exc)[:200]}
         # plain FP32 unfused GPU forward (PyTorch eager, TF32 off): the 5x target's divisor
         from paper_2510_19689_b300.unfused import UnfusedTabNet
-        un = UnfusedTabNet(params, dev)
-        s0 = sets[0]
+        un = UnfusedTabNet(w.params, dev)
+        s0 = w.sets[0]
         for _ in range(3):
             un.forward(s0["xn"], s0["xc"])
         torch.cuda.synchronize()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record()
         for _ in range(10):
             un.forward(s0["xn"], s0["xc"])
         a1.record()
         a1.synchronize()
         un_ms = a0.elapsed_time(a1) / 10
-        extras["fp32_unfused"] = {"value": rows / (un_ms / 1e3), "unit": UNIT, "ms_per_step": un_ms}
+        extras["fp32_unfused"] = {"value": w.rows / (un_ms / 1e3), "unit": UNIT, "ms_per_step": un_ms}
         extras["speedup_vs_fp32_unfused"] = value / world / extras["fp32_unfused"]["value"]
-        # the other precisions of the fused library on the same batch (the
-        # three-part split only where the model shape has it)
-        for prec in ("bf16", "bf16x6", "fp32"):
-            if prec == args.precision:
-                continue
-            try:
-                m2 = tabnet.Model(blob, prec, device=local)
-            except tabnet.TabnetError as exc:
-                extras[f"fused_{prec}"] = {"value": None, "unavailable": str(exc)[:200]}
-                continue
-            if prec != "fp32" and not args.no_tune:
-                autotune.tune(m2, s0["xn"], s0["xc"], rows, s0["lg"], s0["mk"], s0["ag"], stream=stream,
-                              cache_path=None)
-            reps = 20 if prec != "fp32" else 3
-            for _ in range(2):
-                m2.forward(s0["xn"], s0["xc"], rows, s0["lg"], s0["mk"], s0["ag"], stream=stream)
-            b0 = torch.cuda.Event(enable_timing=True)
-            b1 = torch.cuda.Event(enable_timing=True)
-            b0.record(stream)
-            for k in range(reps):
-                s = sets[k % n_sets]
-                m2.forward(s["xn"], s["xc"], rows, s["lg"], s["mk"], s["ag"], stream=stream)
-            b1.record(stream)
-            b1.synchronize()
-            # the same 256 sampled rows against the FP64 oracle
-            m2.forward(s0["xn"], s0["xc"], rows, s0["lg"], s0["mk"], s0["ag"], stream=stream)
-            torch.cuda.synchronize()
-            lg2 = s0["lg"][it].cpu().numpy()
-            mk2 = s0["mk"][it].cpu().numpy()
-            ag2 = s0["ag"][it].cpu().numpy()
-            extras[f"fused_{prec}"] = {
-                "value": rows / (b0.elapsed_time(b1) / reps / 1e3), "unit": UNIT,
-                "parity": {"logit_rel_max": float((np.abs(lg2 - rl) / np.maximum(np.abs(rl), 1)).max()),
-                           "mask_l1_max": float(np.abs(mk2 - rm).sum((1, 2)).max()),
-                           "agg_l1_max": float(np.abs(ag2 - ra).sum(1).max()), "status": m2.poll_status()}}
-            m2.close()
+        del un
+        other_precisions(w, ("bf16", "bf16x6", "fp8", "fp32"), 20, extras)
 
     if rank == 0 and not args.no_extras and args.precision != "fp32":
+        from paper_2510_19689_b300 import tabnet
         # audit statistics over the step's aggregate (mean, variance, top-5
         # frequency per feature): the aggregate read twice plus once per row
-        ag0 = sets[0]["ag"]
+        ag0 = w.sets[0]["ag"]
         for _ in range(3):
-            tabnet.mask_stats(ag0, 5, stream=stream)
+            tabnet.mask_stats(ag0, 5, stream=w.stream)
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
+        a0.record(w.stream)
         for _ in range(20):
-            tabnet.mask_stats(ag0, 5, stream=stream)
-        a1.record(stream)
+            tabnet.mask_stats(ag0, 5, stream=w.stream)
+        a1.record(w.stream)
         a1.synchronize()
         ms_stats = a0.elapsed_time(a1) / 20
-        extras["mask_stats"] = {"ms": ms_stats, "rows_per_s": rows / (ms_stats / 1e3), "k": 5,
-                                "aggregate_bytes": rows * d.n_feat * 4}
+        extras["mask_stats"] = {"ms": ms_stats, "rows_per_s": w.rows / (ms_stats / 1e3), "k": 5,
+                                "aggregate_bytes": w.rows * w.model.dims.n_feat * 4}
 
     if rank == 0 and not args.no_extras and name == "c2":
         # a fresh process's first call (the serverless cold start), on the
@@ -563,24 +702,25 @@ def main():
             except Exception as exc:
                 extras["cold_start"][mode] = {"unavailable": str(exc)[:200]}
 
-    if rank == 0 and not args.no_extras and name == "c3":
-        extras["fp8_gemm_peak"] = fp8_gemm_peak(dev)
-
     if rank == 0 and not args.no_extras and args.precision != "fp32" and name == "c2":
-        extras["batching"] = bench_batching(model, params, dev, stream)
+        extras["batching"] = bench_batching(w.model, w.params, dev, w.stream)
         extras["serving"] = bench_serving(local)
+        # the largest configuration (1,048,576 rows of the 100-input model) in
+        # the same run: split-bf16 and FP8, each with its own roofline, clocks,
+        # end-to-end rate and parity sample, and the oracle's host rate
+        w.close()
+        torch.cuda.empty_cache()
+        extras["c3"] = bench_large("c3", dev, fp8_peak, args)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "ms_per_step_stats": step_stats,
             "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16" if args.precision != "fp32" else "f32", "data": "synthetic",
-            "config": {"workload": describe(name), "rows_per_gpu": rows, "precision": args.precision,
-                       "parallelism": f"replicas x{world} (rows sharded per GPU, no collective)",
-                       "l2": f"{n_sets} rotating input/output sets of {set_bytes / 1e6:.1f} MB "
-                             f"({n_sets * set_bytes / 1e6:.0f} MB > L2)",
-                       "tile": tile},
+            "vs_baseline": None, "dtype": {"fp32": "f32", "fp8": "e4m3"}.get(args.precision, "bf16"),
+            "data": "synthetic",
+            "config": workload_config(name, args.precision, world),
+            "launch_shape": w.tile,
             "gpu_launches": args.steps,
             "clocks": clocks,
             "roofline": roofline,
@@ -588,8 +728,37 @@ def main():
         }
         line.update(extras)
         print(json.dumps(line), flush=True)
-    model.close()
+    if w.sets:
+        w.close()
     group.close()
+
+
+def bench_large(name, dev, fp8_peak, args):
+    """Both fast tensor-core modes on one large workload (one input set per
+    mode beside the first's data)."""
+    import torch
+    from paper_2510_19689_b300 import synth
+    data = synth.load_config(name)
+    out = {"config": workload_config(name, "bf16x3 | fp8", 1), "arms": {}}
+    for prec in ("bf16x3", "fp8"):
+        w = Workload(name, prec, dev, data=data)
+        w.tune()
+        par = w.parity()
+        steps = 10
+        ms, stats, clocks = w.time(steps, 3)
+        ms_step = ms / steps
+        arm = {"value": w.rows * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms_step,
+               "ms_per_step_stats": stats, "tile": w.tile, "clocks": clocks,
+               "roofline": roofline_for(w.params, w.rows, ms_step, prec, False, fp8_peak,
+                                        profiled_traffic(name, prec)),
+               "parity": par, "e2e": w.e2e(steps=5)}
+        if prec == "bf16x3" and not args.no_extras:
+            out["cpu_baseline"] = w.cpu_baseline()
+        out["arms"][prec] = arm
+        w.close()
+        del w
+        torch.cuda.empty_cache()
+    return out
 
 
 if __name__ == "__main__":

@@ -47,19 +47,20 @@ def test_bytes_per_row(name, inp, out):
 
 def test_clock_summary_median_and_reasons():
     c = bench.ClockSampler(0)
-    c.lines = ["2032, 2032, 800.1, 0x0, Not Active, Not Active, Not Active, Not Active",
-               "1980, 2032, 1050.0, 0x4, Not Active, Not Active, Not Active, Active",
-               "2010, 2032, 990.0, 0x0, Not Active, Not Active, Not Active, Not Active",
-               "garbage line",
-               "[N/A], 2032, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    # (sm MHz, max sm MHz, power W, clocks-event reason bits as NVML reports them)
+    c.samples = [(2032.0, 2032.0, 800.1, 0x0), (1980.0, 2032.0, 1050.0, 0x4), (2010.0, 2032.0, 990.0, 0x1),
+                 (1500.0, 2032.0, 700.0, 0x40 | 0x8)]
+    c.how = "test"
     s = c.summary()
-    assert s == {"sm_mhz": 2010.0, "sm_max_mhz": 2032.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert s["sm_mhz"] == 1995.0 and s["sm_min_mhz"] == 1500.0 and s["sm_max_mhz"] == 2032.0
+    assert s["power_w_max"] == 1050.0 and s["samples"] == 4
+    # idle (0x1) is not a throttle reason; power cap, hardware slowdown and thermal are
+    assert s["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_power_cap"]
 
 
 def test_clock_summary_without_samples():
     c = bench.ClockSampler(0)
-    c.lines = []
-    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "how": None}
 
 
 def _fake_root(tmp_path):
