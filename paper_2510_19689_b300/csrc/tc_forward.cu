@@ -28,10 +28,13 @@
 //     loop walks a tile's layers, so there is one MMA issue site.
 //   * Weights stream from L2 through a ring of shared-memory slots filled by
 //     1-D bulk async copies (TMA engine), one part of a K block (128 bytes a
-//     row: 64 bf16 or 128 e4m3 elements) per slot, pre-swizzled by the host.  Thread 0 issues copies and MMAs; each
-//     slot has a "full" barrier (copy landed); a slot read by a layer's last
-//     K block is free once the accumulator barrier fires, earlier blocks'
-//     slots get their own "empty" commit.
+//     row: 64 bf16 or 128 e4m3 elements) per slot, pre-swizzled by the host;
+//     a K block's parts sit in consecutive slots and arrive by one copy (a
+//     copy costs the issuing thread a few hundred cycles when every SM is
+//     copying).  Thread 0 issues copies and MMAs; each such unit has a
+//     "full" barrier (copy landed); a unit read by a layer's last K block is
+//     free once the accumulator barrier fires, earlier blocks' units get
+//     their own "empty" commit.
 //   * Epilogue threads read the accumulator with tcgen05.ld (thread = row),
 //     add the BN shift (the BN scale, -log2(e) for the gate and sqrt(1/2)
 //     for the residual are folded into the packed weights), apply the GLU
@@ -304,26 +307,31 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     const int64_t num_tiles = (total + 127) / 128;
     const int64_t my_tiles =
         (int64_t)blockIdx.x < num_tiles ? (num_tiles - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
+    // The ring holds SU units of PARTS consecutive slots; a unit is one K
+    // block of one layer with all its parts, brought in by one bulk copy (the
+    // parts are contiguous in the weight stream), with one full and one empty
+    // barrier.
+    const int SU = S / PARTS;
     const int64_t total_chunks = my_tiles * p.chunks_per_tile;
     // Ring bookkeeping (thread 0 only), incremental so that no 64-bit
-    // division sits on the MMA critical path: chunk g of the CTA's stream
-    // goes to slot g mod S in round g / S, and is chunk g mod chunks_per_tile
-    // of a tile's sequence.
-    int64_t g_issue = 0, g_cons = 0;  // chunks issued / consumed so far
-    int is_slot = 0, is_chunk = 0;    // slot and per-tile index of chunk g_issue
-    int cs_slot = 0;                  // slot of chunk g_cons
-    uint32_t cs_round = 0;            // round of chunk g_cons
-    // Slots whose release is signalled on their own "empty" barrier (a K
-    // block followed by more blocks of the same layer) and the parity to wait
-    // for; the last block's slots are released by the accumulator barrier.
+    // division sits on the MMA critical path: unit g of the CTA's stream
+    // goes to ring unit g mod SU in round g / SU, and is unit g mod
+    // chunks_per_tile of a tile's sequence.
+    int64_t g_issue = 0, g_cons = 0;  // units issued / consumed so far
+    int is_slot = 0, is_chunk = 0;    // ring unit and per-tile index of unit g_issue
+    int cs_slot = 0;                  // ring unit of unit g_cons
+    uint32_t cs_round = 0;            // round of unit g_cons
+    // Ring units whose release is signalled on their own "empty" barrier (a
+    // K block followed by more blocks of the same layer) and the parity to
+    // wait for; the last block's unit is released by the accumulator barrier.
     uint32_t empty_pending = 0, empty_par = 0;
     bool acc_outstanding = false;
     uint32_t acc_phase = 0;
     int xc = 0;
     int lc = 0;  // layers run by this CTA
 
-    // Thread 0: start the copy of chunk g_issue once its slot is free (the
-    // MMAs that read its previous occupant have completed).
+    // Thread 0: start the copy of unit g_issue once its ring unit is free
+    // (the MMAs that read its previous occupant have completed).
     auto issue_next = [&]() -> bool {
         const int slot = is_slot;
         if (empty_pending & (1u << slot)) {
@@ -336,20 +344,22 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         }
         const uint2 ck = sChunks[is_chunk];
         ptx::mbar_arrive_expect_tx(bar_full + 8 * slot, ck.y);
-        ptx::bulk_g2s(ring_base + (uint32_t)(slot * p.slot_bytes), p.wbase + ck.x, ck.y, bar_full + 8 * slot);
+        ptx::bulk_g2s(ring_base + (uint32_t)(slot * PARTS * p.slot_bytes), p.wbase + ck.x, ck.y, bar_full + 8 * slot);
         ++g_issue;
         if (++is_chunk == p.chunks_per_tile) is_chunk = 0;
-        if (++is_slot == S) is_slot = 0;
+        if (++is_slot == SU) is_slot = 0;
         return true;
     };
     if (tid == 0)
-        while (g_issue < total_chunks && g_issue < S) issue_next();
+        while (g_issue < total_chunks && g_issue < SU) issue_next();
 
     // Publish this thread's A-operand writes and TMEM reads, then let thread 0
     // run one layer's MMA chain (K steps of 16 columns [kbeg, kend) over the
     // 64-wide K blocks that hold them) and wait for the accumulator.
     // Returns false when the CTA has to stop.
-    auto run_mma = [&](int kbeg, int kend, uint32_t idesc) -> bool {
+    // nout: the layer's output rows (its weight block has nout rows of 128
+    // bytes, and the parts of a unit follow each other at that stride).
+    auto run_mma = [&](int kbeg, int kend, uint32_t idesc, int nout) -> bool {
         ptx::fence_proxy_async();
         ptx::tc_fence_before();
         __syncthreads();
@@ -359,25 +369,11 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             bool ok = true;
 #pragma unroll 1
             for (int b = kbeg >> 2; 4 * b < kend && ok; ++b) {
-                while (ok && g_issue < g_cons + PARTS) ok = issue_next();
-                // slots (and rounds) of this K block's hi and lo chunks
-                int slot_p[PARTS];
-                uint32_t round_p[PARTS];
-                {
-                    int sl = cs_slot;
-                    uint32_t rd = cs_round;
-#pragma unroll
-                    for (int part = 0; part < PARTS; ++part) {
-                        slot_p[part] = sl;
-                        round_p[part] = rd;
-                        if (++sl == S) { sl = 0; ++rd; }
-                    }
-                }
-                for (int part = 0; part < PARTS && ok; ++part) {
-                    if (!ptx::mbar_wait(bar_full + 8 * slot_p[part], round_p[part] & 1u, kWaitLimit)) {
-                        note_timeout(m.status, 1, (unsigned)(g_cons + part));
-                        ok = false;
-                    }
+                while (ok && g_issue < g_cons + 1) ok = issue_next();
+                // this K block's unit: its parts in consecutive slots
+                if (ok && !ptx::mbar_wait(bar_full + 8 * cs_slot, cs_round & 1u, kWaitLimit)) {
+                    note_timeout(m.status, 1, (unsigned)g_cons);
+                    ok = false;
                 }
                 if (!ok) break;
                 // descriptors of the block's first K step; a K step of 16
@@ -385,7 +381,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 uint64_t d_b[PARTS], d_a[PARTS];  // part k of W and of A for this K block
 #pragma unroll
                 for (int part = 0; part < PARTS; ++part) {
-                    d_b[part] = ptx::sw128_desc(ring_base + (uint32_t)(slot_p[part] * p.slot_bytes));
+                    d_b[part] = ptx::sw128_desc(ring_base + (uint32_t)(cs_slot * PARTS * p.slot_bytes + part * nout * 128));
                     d_a[part] = ptx::sw128_desc(a_base + (uint32_t)part * a_part + (uint32_t)(b * 16384));
                 }
                 const int k0 = max(kbeg - 4 * b, 0), k1 = min(kend - 4 * b, 4);
@@ -435,17 +431,12 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                         }
                     }
                 }
-#pragma unroll
-                for (int part = 0; part < PARTS; ++part) {
-                    if (4 * (b + 1) < kend) {
-                        ptx::mma_commit(bar_empty + 8 * slot_p[part]);
-                        empty_pending |= 1u << slot_p[part];
-                    }
+                if (4 * (b + 1) < kend) {
+                    ptx::mma_commit(bar_empty + 8 * cs_slot);
+                    empty_pending |= 1u << cs_slot;
                 }
-                g_cons += PARTS;
-#pragma unroll
-                for (int part = 0; part < PARTS; ++part)
-                    if (++cs_slot == S) { cs_slot = 0; ++cs_round; }
+                g_cons += 1;
+                if (++cs_slot == SU) { cs_slot = 0; ++cs_round; }
             }
             ptx::mma_commit(bar_acc);
             acc_outstanding = true;
@@ -473,7 +464,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             if (got) acc_outstanding = false;
             // every MMA so far has completed: refill the free slots
             if (!sAbort[(lc + 1) & 1])
-                while (g_issue < total_chunks && g_issue < g_cons + S)
+                while (g_issue < total_chunks && g_issue < g_cons + SU)
                     if (!issue_next()) { sAbort[(lc + 1) & 1] = 1; break; }
         }
         acc_phase ^= 1;
@@ -739,7 +730,8 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
             // inputs, the others the N outputs of the layer before; the
             // attentive layer reads only the attention half (its weights on
             // the decision half are 0)
-            if (!run_mma(att ? p.att_k0 : 0, (att || !first) ? p.ks_n : p.ks_0, att ? idesc_att : idesc_ft)) {
+            if (!run_mma(att ? p.att_k0 : 0, (att || !first) ? p.ks_n : p.ks_0, att ? idesc_att : idesc_ft,
+                         att ? p.dp : 2 * N)) {
                 alive = false;
                 break;
             }
@@ -1214,11 +1206,11 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         uint32_t rd = cs_round;
         for (int64_t g = g_cons; g < g_issue; ++g) {
             if (!ptx::mbar_wait(bar_full + 8 * sl, rd & 1u, kWaitLimit)) note_timeout(m.status, 3, (unsigned)g);
-            if (++sl == S) { sl = 0; ++rd; }
+            if (++sl == SU) { sl = 0; ++rd; }
         }
         if (acc_outstanding && !ptx::mbar_wait(bar_acc, acc_phase ^ 1, kWaitLimit))
             note_timeout(m.status, 4, (unsigned)lc);
-        for (int sl2 = 0; sl2 < S; ++sl2)
+        for (int sl2 = 0; sl2 < SU; ++sl2)
             if ((empty_pending >> sl2) & 1u)
                 if (!ptx::mbar_wait(bar_empty + 8 * sl2, (empty_par >> sl2) & 1u, kWaitLimit))
                     note_timeout(m.status, 6, (unsigned)sl2);
@@ -1476,17 +1468,24 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
     const int kblock = fp8 ? 128 : 64;  // elements of a K block (128 bytes a row)
     // Every 64-wide K block of W (its parts in order: hi, then lo or mid, lo) becomes a chunk.
     // Blocks before first_block are not streamed (all their weights are 0).
+    bool parts_contiguous = true;
     auto push_layer = [&](const float* W, int n_out, int k_valid, int col_shift, int k_pad, int first_block,
                           std::vector<std::pair<size_t, uint32_t>>* keep) {
         const uint32_t cb = (uint32_t)n_out * 128;
         std::vector<std::vector<uint8_t>> pk(parts);
         for (int part = 0; part < parts; ++part) pack_sw128(W, n_out, k_valid, col_shift, k_pad, part, pk[part]);
         const int blocks = (k_pad + 63) / 64;
-        for (int b = first_block; b < blocks; ++b)
+        for (int b = first_block; b < blocks; ++b) {
+            // one ring unit: the block's parts back to back (cb is a multiple
+            // of 1024, so the arena keeps them contiguous)
+            size_t off0 = 0;
             for (int part = 0; part < parts; ++part) {
                 const size_t off = a.add(pk[part].data() + (size_t)b * cb, cb, 1024);
-                keep->push_back({off, cb});
+                if (part == 0) off0 = off;
+                else if (off != off0 + (size_t)part * cb) parts_contiguous = false;
             }
+            keep->push_back({off0, cb * (uint32_t)parts});
+        }
     };
     // FP8: W' = diag(BN scale) W in double (as the rounding study folds it),
     // quantized per output channel; the kernel's per-channel scale also
@@ -1593,6 +1592,7 @@ int tc_build(tabnet_model* m, Arena& a, std::string* why) {
         m->tc_chunk_off.push_back(c.first);
         m->tc_chunk_bytes.push_back(c.second);
     }
+    if (!parts_contiguous) { *why = "weight stream layout: a K block's parts are not contiguous"; return TABNET_ERR_UNSUPPORTED_DIMS; }
     p.chunks_per_tile = (int)stream.size();
     p.epi_floats = (int)epi.size();
     m->tc_off_epi = a.add(epi.data(), epi.size() * 4, 16);
@@ -1656,6 +1656,7 @@ int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std
             int found = 0;
             for (int sl = 6; sl >= min_slots; --sl) {
                 if (n_slots > 0 && sl != n_slots) continue;
+                if (sl % min_slots) continue;  // whole ring units (a K block's parts)
                 TcSmem sm = smem_layout(N, p.dp, d.d_emb, d.n_feat, d.n_classes, d.n_d, sl, slot_bytes, np, nwg,
                                         p.epi_floats, p.chunks_per_tile, p.tm_agg >= 0, st[0], st[1], st[2]);
                 if ((size_t)sm.total <= budget) { found = sl; break; }

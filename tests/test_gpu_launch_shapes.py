@@ -32,7 +32,11 @@ WIDTHS = {
                           gamma=1.3, n_classes=4),
 }
 ROWS = 3 * 128 + 45
-SHAPES = [(1, 2, 1), (1, 3, 1), (1, 2, 2), (1, 3, 2), (1, 4, 2), (2, 2, 1), (2, 3, 1), (2, 2, 2)]
+# ring depths: a ring holds whole K blocks of every part (2 slots a block in
+# split-bf16, 3 in the three-part split), so some depths exist only for some
+# precisions; 4 and 6 slots give split-bf16 two and three blocks in flight
+SHAPES = [(1, 2, 1), (1, 3, 1), (1, 2, 2), (1, 3, 2), (1, 4, 2), (1, 6, 2), (2, 2, 1), (2, 3, 1), (2, 4, 1),
+          (2, 2, 2)]
 
 
 @pytest.fixture(scope="module")
