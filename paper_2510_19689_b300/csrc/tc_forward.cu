@@ -506,16 +506,35 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 #pragma unroll
         for (int j = 0; j < 16; ++j) mstw[lane * 17 + j] = v[j];
         __syncwarp();
-        const int c = lane & 15;
-        // fully unrolled the row pointers and values of all 16 pieces load
+        // fully unrolled the row pointers and values of all pieces load
         // together (+3 % at 35 inputs); by 4 with two warpgroups, whose
-        // 128-register budget it would otherwise spill
+        // 128-register budget it would otherwise spill.  A piece of at most
+        // 8 (4) columns -- the last of a row -- takes 4 (8) rows a store.
         constexpr int kStageUnroll = NWG == 1 ? 16 : 4;
+        if (ncol > 8) {
+            const int c = lane & 15;
 #pragma unroll kStageUnroll
-        for (int i = 0; i < 16; ++i) {
-            const int r = 2 * i + (lane >> 4);
-            float* dst = rowptr[(warp & 3) * 32 + r];
-            if (dst && c < ncol) dst[base + c] = mstw[r * 17 + c];
+            for (int i = 0; i < 16; ++i) {
+                const int r = 2 * i + (lane >> 4);
+                float* dst = rowptr[(warp & 3) * 32 + r];
+                if (dst && c < ncol) dst[base + c] = mstw[r * 17 + c];
+            }
+        } else if (ncol > 4) {
+            const int c = lane & 7;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int r = 4 * i + (lane >> 3);
+                float* dst = rowptr[(warp & 3) * 32 + r];
+                if (dst && c < ncol) dst[base + c] = mstw[r * 17 + c];
+            }
+        } else {
+            const int c = lane & 3;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = 8 * i + (lane >> 2);
+                float* dst = rowptr[(warp & 3) * 32 + r];
+                if (dst && c < ncol) dst[base + c] = mstw[r * 17 + c];
+            }
         }
         __syncwarp();
     };
