@@ -301,7 +301,11 @@ typedef struct {
 
 /* Create a server over n_models loaded handles (all on one device; the
  * handles must outlive the server).  cfg may be NULL.  Allocates the device
- * rings and their pinned host mirrors and starts the engine thread.
+ * rings and their pinned host mirrors and starts the engine thread.  The
+ * handles' tensor-core launches are resized (same launch shape, more shared
+ * memory where needed) so that CTAs of the different models that the GPU
+ * places on one SM always fit in its tensor memory; this stays in effect for
+ * the handles after the server is destroyed.
  * Errors: ARG, OOM. */
 int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet_server_config* cfg,
                          tabnet_server** out);

@@ -56,6 +56,11 @@ struct tabnet_model {
     // tensor-core path
     tabnet::TcParams tc{};
     tabnet::TcLaunch tc_launch_cfg{};
+    // Set while the model is served next to other models (tabnet_server):
+    // every tensor-core launch then takes shared memory in proportion to its
+    // tensor-memory columns, so that CTAs of different kernels placed on one
+    // SM always fit in its 512 columns.
+    bool tmem_shared = false;
     size_t tc_off_chunks = 0, tc_off_epi = 0, tc_off_colinfo = 0, tc_off_colfeat = 0;
     std::vector<size_t> tc_chunk_off;          // arena offsets of the weight chunks, stream order
     std::vector<uint32_t> tc_chunk_bytes;

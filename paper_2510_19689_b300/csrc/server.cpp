@@ -343,6 +343,16 @@ int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet
     for (int i = 0; i < n_models; ++i) {
         ModelCtx& mc = S->models[i];
         mc.model = models[i];
+        // the models' kernels will share SMs: size their launches so that
+        // co-located CTAs always fit in tensor memory (keeping each launch
+        // shape)
+        if (models[i]->precision != TABNET_FP32 && !models[i]->tmem_shared) {
+            const tabnet::TcLaunch keep = models[i]->tc_launch_cfg;
+            models[i]->tmem_shared = true;
+            std::string why;
+            if (tabnet::tc_choose_launch(models[i], keep.nwg, keep.n_slots, keep.ctas_per_sm, &why) != TABNET_OK)
+                models[i]->tc_launch_cfg = keep;  // the shape no longer fits: keep the old one
+        }
         tabnet_dims_of(models[i], &mc.d);
         mc.in_row = 4 * (size_t)(mc.d.n_num + mc.d.n_cat);
         mc.out_row = 4 * (size_t)(mc.d.n_classes + mc.d.n_steps * mc.d.d_emb + mc.d.n_feat);

@@ -1699,6 +1699,20 @@ int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std
     // request enough shared memory that no more than best_cps CTAs share an SM
     const size_t floor_smem = (size_t)dev_smem_sm / (best_cps + 1) + 1;
     if (smem < floor_smem) smem = std::min(floor_smem, (size_t)m->smem_optin);
+    // The CTA scheduler places CTAs by shared memory, registers and threads,
+    // not by tensor memory, and a CTA whose tcgen05.alloc finds too few free
+    // columns waits until a CTA holding them exits -- after all of that CTA's
+    // tiles, when kernels of other models share the SM.  When the model is
+    // served next to others, a CTA that asks for T of the 512 columns also
+    // takes at least T / 512 of the SM's shared memory (with its reserved
+    // share): then any set of such CTAs the scheduler co-locates fits in
+    // tensor memory.  (Alone, the smaller request leaves more L1 to the
+    // kernels that gather their inputs from global memory: 8 % on the
+    // 100-input FP8 kernel.)
+    if (m->tmem_shared) {
+        const size_t tmem_smem = ((size_t)p.tmem_cols * (size_t)dev_smem_sm + 511) / 512 - (size_t)reserved;
+        if (smem < tmem_smem) smem = std::min(tmem_smem, (size_t)m->smem_optin);
+    }
     m->tc_launch_cfg.nwg = nwg;
     m->tc_launch_cfg.n_slots = best_slots;
     m->tc_launch_cfg.ctas_per_sm = best_cps;
