@@ -61,7 +61,62 @@ struct SimtParams {
     SegTable seg;
     const SimtLayer* ft;   // [(n_steps + 1) * layers_per_ft], FT s layer l at s * lpf + l
     const SimtLayer* att;  // [n_steps]
+    // The warp-per-row kernel's copy of the layers: one unit per layer use
+    // in forward order (feature transformer 0's layers, then for each step
+    // its attentive layer and the next feature transformer's layers), unit u
+    // at row_units + u * row_slot: the weight output-major, [ld][kp] (output
+    // o's k weights contiguous, ld = n_out and kp = k rounded up as
+    // row_r4 / row_kp give, zero-padded), then the BN scale [ld] and shift
+    // [ld].
+    const float* row_units;
+    int row_slot;
 };
+
+#if defined(__CUDACC__)
+#define TABNET_HD __host__ __device__
+#else
+#define TABNET_HD
+#endif
+
+TABNET_HD inline int row_r4(int n) { return (n + 3) & ~3; }
+TABNET_HD inline int row_n_units(int lpf, int n_steps) { return lpf + n_steps * (1 + lpf); }
+// Shape of unit u; *att_step = the step of an attentive unit, else -1, and
+// *ft_layer = the index into SimtParams::ft of a feature-transformer unit.
+TABNET_HD inline void row_unit_shape(int u, int lpf, int de, int N, int n_a, int* k, int* n_out, int* att_step,
+                                     int* ft_layer) {
+    int s = 0, l = u;
+    if (u >= lpf) {
+        const int v = u - lpf, j = v % (1 + lpf);
+        s = v / (1 + lpf) + 1;
+        if (j == 0) {
+            *k = n_a;
+            *n_out = de;
+            *att_step = s - 1;
+            *ft_layer = -1;
+            return;
+        }
+        l = j - 1;
+    }
+    *k = l == 0 ? de : N;
+    *n_out = 2 * N;
+    *att_step = -1;
+    *ft_layer = s * lpf + l;
+}
+// Floats of one unit slot: the largest unit.
+// Row stride of a unit's weight: k rounded up to 4 floats, and to an odd
+// number of 16-byte groups, so that eight consecutive outputs' float4 reads
+// fall in eight different bank groups.
+TABNET_HD inline int row_kp(int k) {
+    const int kp = row_r4(k);
+    return ((kp >> 2) & 1) ? kp : kp + 4;
+}
+// Floats of unit (k, n_out), and of one slot: the largest unit.
+TABNET_HD inline int row_unit_floats(int k, int n_out) { return row_r4(n_out) * (row_kp(k) + 2); }
+TABNET_HD inline int row_slot_floats(int de, int N, int n_a) {
+    const int f0 = row_unit_floats(de, 2 * N), f1 = row_unit_floats(N, 2 * N), fa = row_unit_floats(n_a, de);
+    const int ft = f0 > f1 ? f0 : f1;
+    return ft > fa ? ft : fa;
+}
 
 #ifdef __CUDACC__
 // Total rows of a launch: the batch size, or the last prefix sum.

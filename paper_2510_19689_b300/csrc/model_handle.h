@@ -53,6 +53,7 @@ struct tabnet_model {
     tabnet::SimtParams simt{};
     int simt_rows = 0;
     int simt_max_ctas = 0;
+    int64_t simt_row_max = 0;  // calls of at most this many rows take the warp-per-row kernel
     // tensor-core path
     tabnet::TcParams tc{};
     tabnet::TcLaunch tc_launch_cfg{};

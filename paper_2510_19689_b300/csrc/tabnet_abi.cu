@@ -25,6 +25,18 @@ cudaError_t simt_launch(const SimtParams& p, int rows_per_cta, const float* x_nu
                         int64_t rows, float* logits, float* masks, float* agg, cudaStream_t stream,
                         int max_ctas);
 int simt_occupancy(int rows_per_cta, size_t smem);
+cudaError_t simt_row_configure(size_t smem);
+bool simt_row_plan(const ModelConsts& m, int64_t rows, int num_sms, int w_max, size_t smem_max, int* W, int* nbuf);
+cudaError_t simt_row_launch(const SimtParams& p, const float* x_num, const int* x_cat, int64_t rows, float* logits,
+                            float* masks, float* agg, cudaStream_t stream, int num_sms, int w_max, size_t smem_max);
+// rows per CTA of the warp-per-row kernel at most (one warp each; the kernel
+// caps it at what its launch bounds allow)
+constexpr int kFp32RowWarpsMax = 16;
+// A float32 call of at most this many rows per SM takes the warp-per-row
+// kernel (4,736 rows on 148 SMs).  Measured on B300 at 14, 35 and 100
+// inputs, the warp-per-row kernel is the faster one up to 4-6 K rows and
+// the four-lanes-per-row kernel beyond.
+constexpr int kFp32RowRowsPerSm = 32;
 // segments.cu
 cudaError_t seg_prefix_launch(const tabnet_segment* segs, int n, int64_t* prefix, cudaStream_t stream);
 
@@ -141,6 +153,8 @@ struct SimtLayout {
     struct L { size_t wt, scale, shift; int k, n_out; };
     std::vector<L> ft, att;
     size_t ft_table = 0, att_table = 0;
+    size_t row_units = 0;
+    int row_slot = 0;
 };
 
 void build_simt(const HostModel& hm, Arena& a, SimtLayout& lay) {
@@ -183,6 +197,32 @@ void build_simt(const HostModel& hm, Arena& a, SimtLayout& lay) {
         L.shift = a.add(sh.data(), sh.size() * 4);
         lay.att.push_back(L);
     }
+    // the warp-per-row kernel's unit image (layout in SimtParams)
+    const int lpf = d.n_shared + d.n_indep, n_units = row_n_units(lpf, d.n_steps);
+    const int slot = row_slot_floats(d.d_emb, N, d.n_a);
+    std::vector<float> img((size_t)n_units * slot, 0.f);
+    bool shapes_ok = true;
+    for (int u = 0; u < n_units && shapes_ok; ++u) {
+        int k, n_out, att_step, ft_layer;
+        row_unit_shape(u, lpf, d.d_emb, N, d.n_a, &k, &n_out, &att_step, &ft_layer);
+        const SimtLayout::L& L = att_step >= 0 ? lay.att[att_step] : lay.ft[ft_layer];
+        shapes_ok = L.k == k && L.n_out == n_out;
+        if (!shapes_ok) break;
+        const int ld = row_r4(n_out), kp = row_kp(k);
+        const float* wt = reinterpret_cast<const float*>(a.image.data() + L.wt);
+        const float* sc = reinterpret_cast<const float*>(a.image.data() + L.scale);
+        const float* sh = reinterpret_cast<const float*>(a.image.data() + L.shift);
+        float* dst = img.data() + (size_t)u * slot;
+        for (int o = 0; o < n_out; ++o)
+            for (int kk = 0; kk < k; ++kk) dst[(size_t)o * kp + kk] = wt[(size_t)kk * n_out + o];
+        std::memcpy(dst + (size_t)ld * kp, sc, n_out * sizeof(float));
+        std::memcpy(dst + (size_t)ld * kp + ld, sh, n_out * sizeof(float));
+    }
+    // (row_slot stays 0, and the kernel unused, if a layer had another shape)
+    if (shapes_ok) {
+        lay.row_units = a.add(img.data(), img.size() * sizeof(float), 16);
+        lay.row_slot = slot;
+    }
     lay.ft_table = a.add(nullptr, lay.ft.size() * sizeof(SimtLayer), 16);
     lay.att_table = a.add(nullptr, lay.att.size() * sizeof(SimtLayer), 16);
 }
@@ -203,6 +243,8 @@ void patch_simt(const SimtLayout& lay, Arena& a, const uint8_t* base, SimtParams
     fill(lay.att, lay.att_table);
     p.ft = (const SimtLayer*)(base + lay.ft_table);
     p.att = (const SimtLayer*)(base + lay.att_table);
+    p.row_units = (const float*)(base + lay.row_units);
+    p.row_slot = lay.row_slot;
 }
 
 int check_ptr(const void* p, bool required, const char* name) {
@@ -219,7 +261,13 @@ int forward_impl(tabnet_model* m, const float* x_num, const int32_t* x_cat, int6
     if (m->precision == TABNET_FP32) {
         SimtParams p = m->simt;
         p.seg = seg ? *seg : SegTable{nullptr, nullptr, 0};
-        e = simt_launch(p, m->simt_rows, x_num, x_cat, rows, logits, masks, agg, stream, m->simt_max_ctas);
+        // a call of few rows (known on the host) takes a warp per row, with
+        // results bit for bit those of the four-lanes-per-row kernel
+        if (!seg && rows <= m->simt_row_max)
+            e = simt_row_launch(p, x_num, x_cat, rows, logits, masks, agg, stream, m->num_sms, kFp32RowWarpsMax,
+                                m->smem_optin);
+        else
+            e = simt_launch(p, m->simt_rows, x_num, x_cat, rows, logits, masks, agg, stream, m->simt_max_ctas);
     } else {
         e = tc_launch(m, x_num, x_cat, rows, logits, masks, agg, stream, seg);
     }
@@ -349,6 +397,18 @@ int tabnet_create(const void* blob, size_t blob_bytes, int precision, int device
                 return fail(TABNET_ERR_UNSUPPORTED_DIMS, "model state does not fit in shared memory");
             }
             m->simt_max_ctas = m->num_sms * simt_occupancy(m->simt_rows, simt_smem_bytes(m->consts, m->simt_rows));
+            // warp-per-row form for calls of up to simt_row_max rows (none if
+            // one row and one weight slot exceed shared memory)
+            m->simt_row_max = 0;
+            int row_w = 0, row_nbuf = 0;
+            if (m->simt.row_slot > 0 &&
+                simt_row_plan(m->consts, 1, m->num_sms, kFp32RowWarpsMax, m->smem_optin, &row_w, &row_nbuf)) {
+                if ((e = simt_row_configure(m->smem_optin)) != cudaSuccess) {
+                    tabnet_destroy(m);
+                    return cuda_fail(e, "cudaFuncSetAttribute");
+                }
+                m->simt_row_max = (int64_t)kFp32RowRowsPerSm * m->num_sms;
+            }
         } else {
             rc = tc_patch(m, arena, base, &why);
             if (rc != TABNET_OK) { tabnet_destroy(m); return fail(rc, why); }
