@@ -340,7 +340,7 @@ def fp8_gemm_peak(dev, n=8192, reps=10):
 
 
 def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), seconds=1.0,
-                  streams_per_model=8, max_inflight_batches=32):
+                  streams_per_model=16, max_inflight_batches=32):
     """Poisson arrivals at each rate for `seconds`, request sizes
     floor(exp(U(0, ln 513))) in [1, 512] rows, the three model shapes
     resident (split-bf16), model chosen uniformly; the server's latency
@@ -376,7 +376,41 @@ def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), s
     for m in models:
         m.close()
     return {"models": "14-, 35- and 100-input models resident, split-bf16", "request_rows": "log-uniform 1..512",
+            "server": {"streams_per_model": streams_per_model, "max_inflight_batches": max_inflight_batches,
+                       "batch_min_rows": 512, "batch_wait_us": 200,
+                       "step_masks": "compact (count + column/value slots) for the 35- and 100-input models, "
+                                     "dense for the 14-input one"},
             "rates": out}
+
+
+def bench_latency(dev, calls=200, host_calls=100):
+    """The 14-input model's 1,024-row call (n_d = n_a = 8, 3 steps): per-call
+    device time back to back over rotating input sets, and the latency one
+    synchronous call shows on the host (launch included), for the float32
+    path (its warp-per-row kernel at this size) and split-bf16."""
+    import numpy as np
+    import torch
+    out = {"workload": describe("c1"), "rows_per_call": None, "arms": {}}
+    for prec in ("fp32", "bf16x3"):
+        w = Workload("c1", prec, dev)
+        w.tune()
+        out["rows_per_call"] = w.rows
+        ms, stats, clocks = w.time(calls, 10)
+        lat = []
+        for k in range(host_calls):
+            t0 = time.perf_counter()
+            w.step(k)
+            torch.cuda.synchronize()
+            lat.append(time.perf_counter() - t0)
+        lat = np.array(lat) * 1e3
+        out["arms"][prec] = {"ms_per_call": ms / calls, "ms_per_call_stats": stats,
+                             "rows_per_s": w.rows * calls / (ms / 1e3),
+                             "host_latency_ms": {"p50": float(np.median(lat)), "p99": float(np.quantile(lat, 0.99))},
+                             "tile": w.tile, "clocks": clocks, "parity": w.parity(256)}
+        w.close()
+        del w
+        torch.cuda.empty_cache()
+    return out
 
 
 def spec_params(name):
@@ -691,8 +725,10 @@ def main():
                                 "aggregate_bytes": w.rows * w.model.dims.n_feat * 4}
 
     if rank == 0 and not args.no_extras and name == "c2":
-        # a fresh process's first call (the serverless cold start), on the
-        # paper's model shape (14 inputs, n_d = n_a = 8, 3 steps)
+        # the paper's model shape (14 inputs, n_d = n_a = 8, 3 steps): the
+        # latency of one 1,024-row call, and a fresh process's first call
+        # (the serverless cold start)
+        extras["c1_latency"] = bench_latency(dev)
         extras["cold_start"] = {}
         for mode in ("torch", "notorch"):
             try:

@@ -259,13 +259,15 @@ int tabnet_get_tile_config(const tabnet_model* model, int* nwg, int* n_slots, in
  * A continuous-batching request server over resident models on one GPU (the
  * paper's GPU functions keep the model in GPU memory and serve batches of
  * records per invocation, Sec. III-B, measured by p50/p95/p99 latency,
- * Sec. IV-C).  An engine thread owned by the server packs every request
- * that has arrived for a model into one batch in that model's device ring
- * (admission by device memory: a request waits while the ring is full), runs
- * it as one forward launch with one copy in and one copy out on one of the
- * model's streams, and forms the next batch without waiting, so requests
- * arriving while others run are admitted as memory frees and overlap on the
- * device.  Latency = completion observed on the host - submission. */
+ * Sec. IV-C).  A request's inputs are copied at submission into its
+ * model's pinned input ring (rows in submission order).  An engine thread
+ * owned by the server packs every staged request that has arrived for a
+ * model into one batch (admission by memory: a request waits while a ring is
+ * full), runs it as one forward launch with one copy in and one copy out
+ * on one of the model's streams, and forms the next batch without waiting,
+ * so requests arriving while others run are admitted as memory frees and
+ * overlap on the device.  Latency = completion observed on the host -
+ * submission. */
 typedef struct tabnet_server tabnet_server;
 
 typedef struct {
@@ -279,6 +281,11 @@ typedef struct {
                                   batch of fewer rows than this (0: 512; < 0: off) waits ... */
     int batch_wait_us;         /* ... for more requests, at most this long for its oldest
                                   (0: 200 us), so that one launch serves more rows under load */
+    int mask_slots;            /* step masks go to the host compact: per (row, step) the count of
+                                  nonzero columns and up to this many (column, value) pairs,
+                                  exact; a batch with a row-step over the limit is sent densely.
+                                  0: max(16, d_emb / 5) rounded up to 8 where that saves a quarter
+                                  of the bytes, else dense; < 0: always dense; at most 254 */
 } tabnet_server_config;
 
 typedef struct {
@@ -311,10 +318,12 @@ int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet
                          tabnet_server** out);
 
 /* Queue a request: host inputs [rows, n_num] / [rows, n_cat] of model
- * `model`, which must stay valid until the request is complete.  Returns at
- * once with a ticket.  A request larger than the model's whole ring is
- * rejected by the engine (counted in stats.rejected; it never completes).
- * Thread-safe.  Errors: ARG, OOM. */
+ * `model`, which must stay valid until the request is complete.  Copies the
+ * inputs into the model's input ring when it has room (on the calling
+ * thread; otherwise the engine copies them once room frees) and returns with
+ * a ticket without waiting for the GPU.  A request larger than the model's
+ * rings is rejected by the engine (counted in stats.rejected; it never
+ * completes).  Thread-safe.  Errors: ARG, OOM. */
 int tabnet_server_submit(tabnet_server* server, int model, const float* x_num, const int32_t* x_cat,
                          int64_t rows, uint64_t* ticket);
 
@@ -325,10 +334,22 @@ int tabnet_server_poll(tabnet_server* server, uint64_t* tickets, int max_tickets
 /* Block until the request is complete or timeout_s passes (TIMEOUT). */
 int tabnet_server_wait(tabnet_server* server, uint64_t ticket, double timeout_s);
 
-/* Pointers to a completed request's outputs (pinned host memory owned by the
- * server, laid out as in tabnet_forward), valid until it is released. */
+/* Pointers to a completed request's outputs (host memory owned by the
+ * server, laid out as in tabnet_forward), valid until it is released.  Step
+ * masks that came compact are expanded on the first call, on the calling
+ * thread (call result and release of one ticket from one thread). */
 int tabnet_server_result(tabnet_server* server, uint64_t ticket, const float** logits,
                          const float** step_masks, const float** agg_mask, int64_t* rows);
+
+/* The step masks of a completed request in the compact form they came in:
+ * for (row i, step s) at k = i n_steps + s, counts[k] nonzero columns, the
+ * first min(counts[k], slots) of them at cols[k slots + j] (ascending) with
+ * values vals[k slots + j]; every other entry is +0.  *slots = 0 and NULL
+ * pointers when the request's batch was sent densely (read it through
+ * tabnet_server_result).  Valid until the request is released.
+ * Errors: ARG. */
+int tabnet_server_result_compact(tabnet_server* server, uint64_t ticket, const uint8_t** counts,
+                                 const uint16_t** cols, const float** vals, int* slots, int64_t* rows);
 
 /* Give a completed request's result memory back (ring space is reused once
  * every request of its batch and of older batches is released). */

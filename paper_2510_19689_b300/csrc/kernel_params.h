@@ -14,6 +14,10 @@ struct SegTable {
     const tabnet_segment* segs;  // [n] device copy of the descriptors
     const int64_t* prefix;       // [n + 1] exclusive prefix sums of the rows
     int n;
+    // 4-byte words from one input row to the next, for x_num and x_cat
+    // alike (rows whose numeric and categorical columns are interleaved in
+    // one buffer); 0: dense, n_num and n_cat words
+    int in_stride = 0;
 };
 
 // Where one packed row reads its inputs and writes its outputs.
@@ -147,8 +151,8 @@ __device__ __forceinline__ RowIO row_io(const SegTable& t, const ModelConsts& m,
         masks = sg.step_masks;
         agg = sg.agg_mask;
     }
-    io.x_num = x_num ? x_num + r * m.n_num : nullptr;
-    io.x_cat = x_cat ? x_cat + r * m.n_cat : nullptr;
+    io.x_num = x_num ? x_num + r * (t.in_stride ? t.in_stride : m.n_num) : nullptr;
+    io.x_cat = x_cat ? x_cat + r * (t.in_stride ? t.in_stride : m.n_cat) : nullptr;
     io.logits = logits + r * m.n_classes;
     io.masks = masks ? masks + r * (int64_t)m.n_steps * m.de : nullptr;
     io.agg = agg ? agg + r * m.d : nullptr;

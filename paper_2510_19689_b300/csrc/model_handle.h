@@ -89,6 +89,8 @@ cudaError_t tc_launch(tabnet_model* m, const float* x_num, const int* x_cat, int
                       float* logits, float* masks, float* agg, cudaStream_t stream,
                       const SegTable* seg = nullptr);
 void tc_release(tabnet_model* m);
+int forward_interleaved(tabnet_model* m, const void* rows_in, int64_t rows, float* logits, float* step_masks,
+                        float* agg_mask, cudaStream_t stream);
 int tc_choose_launch(tabnet_model* m, int nwg, int n_slots, int ctas_per_sm, std::string* why);
 
 }  // namespace tabnet

@@ -5,24 +5,31 @@
 // (Sec. III-B), reporting p50/p95/p99 latency beside throughput (Sec. IV-C).
 // This engine does that for many concurrent requests on one GPU:
 //
-//   * every model has a device ring buffer and a pinned host mirror of the
-//     same size (its share of the memory budget); a batch occupies one
-//     contiguous region of the ring: all inputs, then all outputs;
-//   * an engine thread takes, per model, every request that has arrived
-//     (up to max_batch_rows) and packs it into the next region the ring can
-//     hold -- admission is by device memory: a request waits while its
-//     model's ring is full and is rejected only if it could never fit;
-//   * the batch is copied in with one host-to-device copy, run as ONE
-//     forward launch over its packed rows, and copied out with one
-//     device-to-host copy, on one of the model's streams; the engine never
-//     waits for a batch before forming the next one, so requests that arrive
-//     while others are on the GPU are admitted as soon as ring space frees
-//     and their batches overlap on the device (streams of other batches and
-//     of the other models);
-//   * completion is observed by polling the batch's event; the request's
-//     results stay in the pinned mirror until the caller releases it, and a
-//     region is reused once its batch and every older batch of the ring are
-//     released.
+//   * every model has two device rings with pinned host mirrors (its share
+//     of the memory budget, split so both hold about as many rows): an
+//     input ring of rows, filled in submission order, and an output ring of
+//     bytes with one contiguous region per batch;
+//   * a request's inputs are copied into the input ring by the submitting
+//     thread when the ring has room (and no older request of the model is
+//     still waiting for room), otherwise by the engine later, in order --
+//     admission is by memory: a request waits while a ring is full and is
+//     rejected only if it could never fit.  The copies stay off the engine
+//     thread, whose time per request is what bounds the request rate;
+//   * an engine thread takes, per model, every staged request that has
+//     arrived (up to max_batch_rows; consecutive requests are consecutive
+//     input rows) into one batch: one host-to-device copy of its rows, ONE
+//     forward launch over them, and one device-to-host copy of the outputs,
+//     on one of the model's streams (the copy engines, not the kernels, are
+//     what saturates first at high request rates: each copy counts); the
+//     engine never waits for a batch before forming the next one, so
+//     requests that arrive while others are on the GPU are admitted as soon
+//     as ring space frees and their batches overlap on the device (streams
+//     of other batches and of the other models);
+//   * completion is observed by polling the batch's event (a batch found
+//     running is asked again 10 us later); its input rows go back at once,
+//     the request's results stay in the pinned output mirror until the
+//     caller releases it, and an output region is reused once its batch and
+//     every older batch of the ring are released.
 // Latency of a request = completion observed on the host - submission time.
 #include <cuda_runtime.h>
 
@@ -43,6 +50,8 @@
 
 namespace tabnet {
 int set_last_error(int code, const std::string& why);
+cudaError_t mask_compact_launch(const float* masks, int64_t row_steps, int de, int slots, uint8_t* counts,
+                                uint16_t* cols, float* vals, cudaStream_t stream);
 }
 
 namespace {
@@ -50,12 +59,18 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 struct Request {
-    uint64_t ticket;
-    int model;
-    const float* x_num;
-    const int32_t* x_cat;
-    int64_t rows;
+    uint64_t ticket = 0;
+    int model = 0;
+    const float* x_num = nullptr;
+    const int32_t* x_cat = nullptr;
+    int64_t rows = 0;
     Clock::time_point t_submit;
+    // rows of the model's input ring holding the inputs (-1: not staged
+    // yet), and whether they are copied there
+    int64_t in_row0 = -1;
+    std::atomic<bool> ready{false};
+    // the dense step masks, expanded from the compact form on first request
+    std::vector<float> dense_masks;
     // filled when batched
     int64_t row0 = 0;       // first row inside its batch
     struct Batch* batch = nullptr;
@@ -64,9 +79,16 @@ struct Request {
 struct Batch {
     int model;
     int stream_idx;
-    size_t off = 0, bytes = 0;  // ring region
+    size_t off = 0, bytes = 0;  // output ring region
     int64_t rows = 0;
-    size_t in_num = 0, in_cat = 0, out_lg = 0, out_mk = 0, out_ag = 0;  // offsets inside the region
+    int64_t in_row0 = 0;        // input ring rows [in_row0, in_row0 + rows)
+    Clock::time_point next_query;  // no completion query before this
+    // offsets inside the output region: logits, aggregate, then (compact
+    // transfer) counts, columns and values, then the dense step masks; the
+    // first copy_bytes go to the host, the dense masks too when dense
+    size_t out_lg = 0, out_ag = 0, out_cnt = 0, out_col = 0, out_val = 0, out_mk = 0, copy_bytes = 0;
+    bool dense = true;          // the host mirror holds the dense step masks
+    bool dense_pending = false; // a row-step overflowed its slots: the dense copy is on its way
     std::vector<uint64_t> tickets;
     cudaEvent_t done = nullptr;
     Clock::time_point t_launch;
@@ -74,14 +96,30 @@ struct Batch {
     int released = 0;
 };
 
+// A ring of `cap` units: allocate at head, free at tail, in order.
+struct Ring {
+    size_t cap = 0, head = 0, tail = 0, used = 0;
+};
+
 struct ModelCtx {
     tabnet_model* model;
     tabnet_dims d;
     size_t in_row, out_row;        // bytes per row (inputs, outputs)
+    // outputs: a ring of bytes, one region per batch
     uint8_t* dev = nullptr;        // device ring
     uint8_t* host = nullptr;       // pinned mirror
-    size_t cap = 0, head = 0, tail = 0, used = 0;  // ring: allocate at head, free at tail
-    std::deque<Batch*> inflight;   // in ring order
+    Ring out;
+    // inputs: a ring of rows, requests in submission order (so a batch of
+    // consecutive requests is one row range, one copy); row i at
+    // in_* + i in_row: its n_num floats, then its n_cat codes
+    uint8_t* in_dev = nullptr;
+    uint8_t* in_host = nullptr;
+    Ring in;
+    int slots = 0;                 // compact mask slots per (row, step); 0: dense transfer
+    int64_t stage_max = 0;         // rows a request may have to be staged (fits both rings)
+    int64_t unstaged = 0;          // queued requests whose inputs are not in the input ring yet
+    std::deque<Batch*> in_order;   // batches holding input rows, in ring order
+    std::deque<Batch*> inflight;   // in output-ring order
     std::deque<Request*> pending;
     std::vector<cudaStream_t> streams;
     int next_stream = 0;
@@ -90,6 +128,8 @@ struct ModelCtx {
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+constexpr size_t kRegionSlack = 6 * 256;  // alignment of the six arrays of an output region
 
 }  // namespace
 
@@ -106,6 +146,7 @@ struct tabnet_server {
     Clock::time_point t_reset = Clock::now();
     std::thread engine;
     std::atomic<bool> stop{false};
+    std::atomic<bool> engine_idle{false};  // the engine sleeps on cv: submit and release wake it
     int device = 0;
     int error = TABNET_OK;
     std::vector<cudaEvent_t> free_events;  // completion events of freed batches, reused (engine thread only)
@@ -113,42 +154,69 @@ struct tabnet_server {
 
 namespace {
 
-// Reserve `bytes` contiguous bytes at the ring head (wrapping to 0 when the
-// tail leaves room there).  Returns false when the ring cannot hold them now.
-bool ring_alloc(ModelCtx& mc, size_t bytes, size_t* off) {
-    if (bytes > mc.cap) return false;
-    if (mc.used == 0) mc.head = mc.tail = 0;
-    if (mc.head >= mc.tail && mc.used < mc.cap) {
-        if (mc.cap - mc.head >= bytes) { *off = mc.head; mc.head += bytes; mc.used += bytes; return true; }
-        if (mc.tail >= bytes) {  // wrap: waste the end of the ring
-            mc.used += (mc.cap - mc.head) + bytes;
+// Offsets of a batch's output region (see Batch).
+void layout_region(const ModelCtx& mc, Batch* b) {
+    const tabnet_dims& d = mc.d;
+    const size_t rs = (size_t)b->rows * d.n_steps;
+    b->out_lg = 0;
+    b->out_ag = b->out_lg + align256((size_t)b->rows * d.n_classes * 4);
+    b->out_cnt = b->out_ag + align256((size_t)b->rows * d.n_feat * 4);
+    b->out_col = b->out_cnt + (mc.slots ? align256(rs) : 0);
+    b->out_val = b->out_col + (mc.slots ? align256(rs * mc.slots * 2) : 0);
+    b->out_mk = b->out_val + (mc.slots ? align256(rs * mc.slots * 4) : 0);
+    b->copy_bytes = mc.slots ? b->out_mk : b->out_mk + rs * d.d_emb * 4;
+    b->dense = mc.slots == 0;
+}
+
+// Reserve n contiguous units at the ring head (wrapping to 0 when the tail
+// leaves room there).  Returns false when the ring cannot hold them now.
+bool ring_alloc(Ring& g, size_t n, size_t* off) {
+    if (n > g.cap) return false;
+    if (g.used == 0) g.head = g.tail = 0;
+    if (g.head >= g.tail && g.used < g.cap) {
+        if (g.cap - g.head >= n) { *off = g.head; g.head += n; g.used += n; return true; }
+        if (g.tail >= n) {  // wrap: waste the end of the ring
+            g.used += (g.cap - g.head) + n;
             *off = 0;
-            mc.head = bytes;
+            g.head = n;
             return true;
         }
         return false;
     }
-    if (mc.head < mc.tail && mc.tail - mc.head >= bytes) { *off = mc.head; mc.head += bytes; mc.used += bytes; return true; }
+    if (g.head < g.tail && g.tail - g.head >= n) { *off = g.head; g.head += n; g.used += n; return true; }
     return false;
 }
 
-// Free the oldest batch's region (regions are released in ring order).
-void ring_free_front(ModelCtx& mc) {
-    Batch* b = mc.inflight.front();
-    const size_t end = b->off + b->bytes;
-    if (b->off < mc.tail) {  // this batch wrapped: the waste before it goes too
-        mc.used -= (mc.cap - mc.tail);
-        mc.tail = 0;
+// Free the oldest allocation, [off, off + n) (allocations are freed in ring
+// order).
+void ring_free_front(Ring& g, size_t off, size_t n) {
+    if (off < g.tail) {  // this allocation wrapped: the waste before it goes too
+        g.used -= (g.cap - g.tail);
+        g.tail = 0;
     }
-    mc.used -= b->bytes;
-    mc.tail = end;
-    if (mc.used == 0) mc.head = mc.tail = 0;
-    mc.inflight.pop_front();
+    g.used -= n;
+    g.tail = off + n;
+    if (g.used == 0) g.head = g.tail = 0;
+}
+
+// Copy a request's inputs into its input-ring rows (pinned host memory),
+// each row's numeric columns then its categorical codes.
+void stage_inputs(ModelCtx& mc, Request* r) {
+    const tabnet_dims& d = mc.d;
+    const size_t nb = (size_t)d.n_num * 4, cb = (size_t)d.n_cat * 4;
+    uint8_t* dst = mc.in_host + (size_t)r->in_row0 * mc.in_row;
+    const uint8_t* xn = reinterpret_cast<const uint8_t*>(r->x_num);
+    const uint8_t* xc = reinterpret_cast<const uint8_t*>(r->x_cat);
+    for (int64_t i = 0; i < r->rows; ++i, dst += mc.in_row) {
+        if (nb) std::memcpy(dst, xn + i * nb, nb);
+        if (cb) std::memcpy(dst + nb, xc + i * cb, cb);
+    }
+    r->ready.store(true, std::memory_order_release);
 }
 
 void engine_loop(tabnet_server* S) {
     cudaSetDevice(S->device);
-    std::vector<Request*> take;
+    std::vector<Request*> take, stage_now;
     while (!S->stop.load(std::memory_order_relaxed)) {
         bool did = false;
         // 1. completions: batches of one stream finish in order, batches of
@@ -164,15 +232,41 @@ void engine_loop(tabnet_server* S) {
                 const uint64_t bit = 1ull << (b->stream_idx & 63);
                 if (blocked & bit) continue;
                 // no batch completes within 20 us of its launch (copies and
-                // one kernel): do not spend a query on it
-                if (t_now - b->t_launch < std::chrono::microseconds(20)) {
+                // one kernel), and one found running is asked again 10 us
+                // later: a query costs the engine about a microsecond
+                if (t_now < b->next_query) {
                     blocked |= bit;
                     continue;
                 }
                 const cudaError_t q = cudaEventQuery(b->done);
                 if (q == cudaErrorNotReady) {
+                    b->next_query = t_now + std::chrono::microseconds(10);
                     blocked |= bit;
                     continue;
+                }
+                if (q == cudaSuccess && !b->dense) {
+                    if (b->dense_pending) {
+                        b->dense = true;  // the dense copy has arrived
+                    } else {
+                        // a row-step with more nonzeros than slots: send this
+                        // batch's dense masks too (rare: the slots are sized
+                        // well above the supports sparsemax produces)
+                        const uint8_t* cnt = mc.host + b->off + b->out_cnt;
+                        const size_t rs = (size_t)b->rows * mc.d.n_steps;
+                        bool over = false;
+                        for (size_t i = 0; i < rs && !over; ++i) over = cnt[i] > mc.slots;
+                        if (over) {
+                            const size_t mk_bytes = rs * mc.d.d_emb * 4;
+                            cudaStream_t st = mc.streams[b->stream_idx];
+                            cudaMemcpyAsync(mc.host + b->off + b->out_mk, mc.dev + b->off + b->out_mk, mk_bytes,
+                                            cudaMemcpyDeviceToHost, st);
+                            cudaEventRecord(b->done, st);
+                            b->dense_pending = true;
+                            b->next_query = t_now + std::chrono::microseconds(10);
+                            blocked |= bit;
+                            continue;
+                        }
+                    }
                 }
                 const auto now = Clock::now();
                 std::lock_guard<std::mutex> lk(S->mu);
@@ -189,22 +283,32 @@ void engine_loop(tabnet_server* S) {
                 if (q != cudaSuccess && S->error == TABNET_OK) S->error = TABNET_ERR_CUDA;
                 did = true;
             }
-            // free released batches at the front of the ring
             std::lock_guard<std::mutex> lk(S->mu);
+            // input rows of finished batches go back at once, in ring order
+            while (!mc.in_order.empty() && mc.in_order.front()->complete) {
+                Batch* b = mc.in_order.front();
+                ring_free_front(mc.in, (size_t)b->in_row0, (size_t)b->rows);
+                mc.in_order.pop_front();
+                did = true;
+            }
+            // output regions once every request of the batch is released
             while (!mc.inflight.empty() && mc.inflight.front()->complete &&
                    mc.inflight.front()->released == (int)mc.inflight.front()->tickets.size()) {
                 Batch* b = mc.inflight.front();
-                ring_free_front(mc);
+                ring_free_front(mc.out, b->off, b->bytes);
+                mc.inflight.pop_front();
                 S->free_events.push_back(b->done);
                 delete b;
                 did = true;
             }
         }
         if (did) S->cv.notify_all();
-        // 2. form and launch batches: everything pending that fits
+        // 2. form and launch batches: consecutive staged requests, as many as fit
         for (int mi = 0; mi < (int)S->models.size(); ++mi) {
             ModelCtx& mc = S->models[mi];
+            const tabnet_dims& d = mc.d;
             take.clear();
+            stage_now.clear();
             int64_t rows = 0;
             size_t off = 0, bytes = 0;
             {
@@ -218,54 +322,66 @@ void engine_loop(tabnet_server* S) {
                     mc.pending_rows < S->cfg.batch_min_rows &&
                     Clock::now() - mc.pending.front()->t_submit < std::chrono::microseconds(S->cfg.batch_wait_us))
                     continue;
+                int64_t next_row = -1;  // the input row the batch continues at
                 while (!mc.pending.empty()) {
                     Request* r = mc.pending.front();
-                    const int64_t nr = rows + r->rows;
-                    if (!take.empty() && nr > S->cfg.max_batch_rows) break;
-                    const size_t need = 5 * 256 + (size_t)nr * (mc.in_row + mc.out_row);
-                    if (need > mc.cap) {
-                        if (take.empty()) {  // could never fit: reject
+                    if (r->in_row0 < 0) {
+                        // not staged at submission (the input ring was full then)
+                        if (r->rows > mc.stage_max) {
+                            if (!take.empty()) break;
+                            // could never fit: reject
                             mc.pending.pop_front();
                             mc.pending_rows -= r->rows;
+                            --mc.unstaged;
                             S->reqs.erase(r->ticket);
                             ++S->rejected;
                             delete r;
                             continue;
                         }
-                        break;
+                        size_t row0 = 0;
+                        if (!ring_alloc(mc.in, (size_t)r->rows, &row0)) break;  // admission waits for memory
+                        r->in_row0 = (int64_t)row0;
+                        --mc.unstaged;
+                        stage_now.push_back(r);  // copied below, outside the lock
+                    } else if (!r->ready.load(std::memory_order_acquire)) {
+                        break;  // its submitter is still copying the inputs
                     }
+                    if (next_row >= 0 && r->in_row0 != next_row) break;  // the input ring wrapped
+                    const int64_t nr = rows + r->rows;
+                    if (!take.empty() && nr > S->cfg.max_batch_rows) break;
+                    if (align256(kRegionSlack + (size_t)nr * mc.out_row) > mc.out.cap) break;
                     take.push_back(r);
                     rows = nr;
+                    next_row = r->in_row0 + r->rows;
                     mc.pending.pop_front();
                     mc.pending_rows -= r->rows;
                 }
-                if (take.empty()) continue;
-                bytes = 5 * 256 + (size_t)rows * (mc.in_row + mc.out_row);
-                if (!ring_alloc(mc, bytes, &off)) {  // no room now: admission waits for memory
-                    for (auto it = take.rbegin(); it != take.rend(); ++it) {
-                        mc.pending.push_front(*it);
-                        mc.pending_rows += (*it)->rows;
+                if (!take.empty()) {
+                    // whole 256-byte units, so that every region starts aligned
+                    bytes = align256(kRegionSlack + (size_t)rows * mc.out_row);
+                    if (!ring_alloc(mc.out, bytes, &off)) {  // no room now: admission waits for memory
+                        for (auto it = take.rbegin(); it != take.rend(); ++it) {
+                            mc.pending.push_front(*it);
+                            mc.pending_rows += (*it)->rows;
+                        }
+                        take.clear();
                     }
-                    continue;
                 }
             }
-            const tabnet_dims& d = mc.d;
+            // requests staged by the engine (every one of them is in `take`
+            // or at the front of the queue): copy, then mark ready
+            for (Request* r : stage_now) stage_inputs(mc, r);
+            if (!stage_now.empty()) did = true;
+            if (take.empty()) continue;
             Batch* b = new Batch();
             b->model = mi;
             b->off = off;
             b->bytes = bytes;
             b->rows = rows;
-            b->in_num = 0;
-            b->in_cat = align256((size_t)rows * d.n_num * 4);
-            b->out_lg = b->in_cat + align256((size_t)rows * d.n_cat * 4);
-            b->out_mk = b->out_lg + align256((size_t)rows * d.n_classes * 4);
-            b->out_ag = b->out_mk + align256((size_t)rows * d.n_steps * d.d_emb * 4);
-            const size_t in_bytes = b->out_lg;
-            uint8_t* h = mc.host + off;
+            b->in_row0 = take.front()->in_row0;
+            layout_region(mc, b);
             int64_t r0 = 0;
             for (Request* r : take) {
-                if (d.n_num) std::memcpy(h + b->in_num + (size_t)r0 * d.n_num * 4, r->x_num, (size_t)r->rows * d.n_num * 4);
-                if (d.n_cat) std::memcpy(h + b->in_cat + (size_t)r0 * d.n_cat * 4, r->x_cat, (size_t)r->rows * d.n_cat * 4);
                 r->row0 = r0;
                 r->batch = b;
                 b->tickets.push_back(r->ticket);
@@ -274,24 +390,31 @@ void engine_loop(tabnet_server* S) {
             b->stream_idx = mc.next_stream;
             mc.next_stream = (mc.next_stream + 1) % (int)mc.streams.size();
             cudaStream_t st = mc.streams[b->stream_idx];
-            uint8_t* dv = mc.dev + off;
             if (!S->free_events.empty()) {
                 b->done = S->free_events.back();
                 S->free_events.pop_back();
             } else {
                 cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
             }
-            cudaMemcpyAsync(dv, h, in_bytes, cudaMemcpyHostToDevice, st);
-            int rc = tabnet_forward(mc.model, d.n_num ? (const float*)(dv + b->in_num) : nullptr,
-                                    d.n_cat ? (const int32_t*)(dv + b->in_cat) : nullptr, rows,
-                                    (float*)(dv + b->out_lg), (float*)(dv + b->out_mk), (float*)(dv + b->out_ag), st);
-            cudaMemcpyAsync(h + b->out_lg, dv + b->out_lg, b->bytes - b->out_lg - 0, cudaMemcpyDeviceToHost, st);
+            const size_t in0 = (size_t)b->in_row0 * mc.in_row;
+            cudaMemcpyAsync(mc.in_dev + in0, mc.in_host + in0, (size_t)rows * mc.in_row, cudaMemcpyHostToDevice, st);
+            uint8_t* dv = mc.dev + off;
+            int rc = tabnet::forward_interleaved(mc.model, mc.in_dev + in0, rows, (float*)(dv + b->out_lg),
+                                                 (float*)(dv + b->out_mk), (float*)(dv + b->out_ag), st);
+            if (mc.slots && rc == TABNET_OK &&
+                tabnet::mask_compact_launch((const float*)(dv + b->out_mk), rows * d.n_steps, d.d_emb, mc.slots,
+                                            dv + b->out_cnt, (uint16_t*)(dv + b->out_col), (float*)(dv + b->out_val),
+                                            st) != cudaSuccess)
+                rc = TABNET_ERR_CUDA;
+            cudaMemcpyAsync(mc.host + off, dv, b->copy_bytes, cudaMemcpyDeviceToHost, st);
             cudaEventRecord(b->done, st);
             b->t_launch = Clock::now();
+            b->next_query = b->t_launch + std::chrono::microseconds(20);
             {
                 std::lock_guard<std::mutex> lk(S->mu);
                 if (rc != TABNET_OK && S->error == TABNET_OK) S->error = rc;
                 mc.inflight.push_back(b);
+                mc.in_order.push_back(b);
                 ++mc.running;
                 ++S->batches;
                 S->batch_rows += rows;
@@ -300,7 +423,9 @@ void engine_loop(tabnet_server* S) {
         }
         if (!did) {
             std::unique_lock<std::mutex> lk(S->mu);
+            S->engine_idle.store(true, std::memory_order_relaxed);
             S->cv.wait_for(lk, std::chrono::microseconds(50));
+            S->engine_idle.store(false, std::memory_order_relaxed);
         }
     }
 }
@@ -321,6 +446,7 @@ int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet
     S->cfg.streams_per_model = cfg && cfg->streams_per_model > 0 ? std::min(cfg->streams_per_model, 64) : 8;
     S->cfg.batch_min_rows = cfg && cfg->batch_min_rows != 0 ? cfg->batch_min_rows : 512;
     S->cfg.batch_wait_us = cfg && cfg->batch_wait_us > 0 ? cfg->batch_wait_us : 200;
+    S->cfg.mask_slots = cfg ? cfg->mask_slots : 0;
     S->device = models[0]->device;
     int prev = 0;
     cudaGetDevice(&prev);
@@ -355,11 +481,33 @@ int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet
         }
         tabnet_dims_of(models[i], &mc.d);
         mc.in_row = 4 * (size_t)(mc.d.n_num + mc.d.n_cat);
-        mc.out_row = 4 * (size_t)(mc.d.n_classes + mc.d.n_steps * mc.d.d_emb + mc.d.n_feat);
-        mc.cap = (size_t)(S->cfg.device_bytes * (w[i] / wsum)) / 256 * 256;
-        cudaError_t e1 = cudaMalloc(&mc.dev, mc.cap);
-        cudaError_t e2 = cudaHostAlloc(&mc.host, mc.cap, cudaHostAllocDefault);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        // compact mask transfer: `slots` (column, value) pairs per row-step;
+        // by default max(16, de / 5) rounded up to 8 -- well above the
+        // supports sparsemax gives (at most 25 of 160 columns, 13 of 35 on
+        // the synthetic workloads) -- where that is at most 3/4 of the dense
+        // bytes; a row-step with more sends its batch densely
+        const int de = mc.d.d_emb;
+        int slots = S->cfg.mask_slots;
+        if (slots == 0) {
+            slots = (std::max(16, (de + 4) / 5) + 7) / 8 * 8;
+            if (1 + 6 * slots > 3 * de) slots = 0;
+        }
+        // (a count saturates at 255, so 255 itself always reads as overflow)
+        mc.slots = slots < 0 ? 0 : std::min(slots, 254);
+        mc.out_row = 4 * (size_t)(mc.d.n_classes + mc.d.n_steps * de + mc.d.n_feat) +
+                     (mc.slots ? (size_t)mc.d.n_steps * (1 + 6 * (size_t)mc.slots) : 0);
+        // the model's share, split so that both rings hold about as many rows
+        const size_t share = (size_t)(S->cfg.device_bytes * (w[i] / wsum));
+        const size_t ring_rows = share / (mc.in_row + mc.out_row);
+        mc.out.cap = (ring_rows * mc.out_row + kRegionSlack) / 256 * 256;
+        mc.in.cap = ring_rows;
+        const size_t in_bytes = align256(ring_rows * mc.in_row);
+        mc.stage_max = (int64_t)std::min(ring_rows, (mc.out.cap - kRegionSlack - 256) / mc.out_row);
+        cudaError_t e1 = cudaMalloc(&mc.dev, mc.out.cap);
+        cudaError_t e2 = cudaHostAlloc(&mc.host, mc.out.cap, cudaHostAllocDefault);
+        cudaError_t e3 = cudaMalloc(&mc.in_dev, in_bytes);
+        cudaError_t e4 = cudaHostAlloc(&mc.in_host, in_bytes, cudaHostAllocDefault);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess || ring_rows == 0) {
             tabnet_server_destroy(S);
             cudaSetDevice(prev);
             return tabnet::set_last_error(TABNET_ERR_OOM, "server ring allocation failed");
@@ -379,17 +527,39 @@ int tabnet_server_submit(tabnet_server* S, int model, const float* x_num, const 
         return tabnet::set_last_error(TABNET_ERR_ARG, "bad server, model index, rows or ticket pointer");
     const tabnet_dims& d = S->models[model].d;
     if ((d.n_num && !x_num) || (d.n_cat && !x_cat)) return tabnet::set_last_error(TABNET_ERR_ARG, "null input");
-    Request* r = new (std::nothrow) Request{0, model, x_num, x_cat, rows, Clock::now()};
+    Request* r = new (std::nothrow) Request();
     if (!r) return tabnet::set_last_error(TABNET_ERR_OOM, "host allocation failed");
+    r->model = model;
+    r->x_num = x_num;
+    r->x_cat = x_cat;
+    r->rows = rows;
+    r->t_submit = Clock::now();
     r->ticket = S->next_ticket.fetch_add(1);
+    bool staged = false;
+    ModelCtx& mc = S->models[model];
     {
         std::lock_guard<std::mutex> lk(S->mu);
         S->reqs.emplace(r->ticket, r);
-        S->models[model].pending.push_back(r);
-        S->models[model].pending_rows += rows;
+        // the inputs go to the input ring now, in submission order, unless
+        // an older request is still waiting for room there (then the engine
+        // copies this one later, in order)
+        size_t row0 = 0;
+        if (mc.unstaged == 0 && rows <= mc.stage_max && ring_alloc(mc.in, (size_t)rows, &row0)) {
+            r->in_row0 = (int64_t)row0;
+            staged = true;
+        } else {
+            ++mc.unstaged;
+        }
+        mc.pending.push_back(r);
+        mc.pending_rows += rows;
         ++S->submitted;
     }
-    S->cv.notify_all();
+    // the copy runs on the submitting thread, outside the lock; the engine
+    // takes the request into a batch once it is marked ready
+    if (staged) stage_inputs(mc, r);
+    // a wake-up only when the engine sleeps (a missed one costs at most its
+    // 50 us nap): a notify is a system call, and submit runs per request
+    if (S->engine_idle.load(std::memory_order_relaxed)) S->cv.notify_all();
     *ticket = r->ticket;
     return TABNET_OK;
 }
@@ -409,35 +579,107 @@ int tabnet_server_poll(tabnet_server* S, uint64_t* tickets, int max_tickets, int
 int tabnet_server_result(tabnet_server* S, uint64_t ticket, const float** logits, const float** step_masks,
                          const float** agg_mask, int64_t* rows) {
     if (!S) return tabnet::set_last_error(TABNET_ERR_ARG, "null server");
-    std::lock_guard<std::mutex> lk(S->mu);
-    auto it = S->reqs.find(ticket);
-    if (it == S->reqs.end() || !it->second->batch || !it->second->batch->complete)
-        return tabnet::set_last_error(TABNET_ERR_ARG, "ticket unknown, released or not complete");
-    Request* r = it->second;
-    Batch* b = r->batch;
-    const ModelCtx& mc = S->models[r->model];
-    const tabnet_dims& d = mc.d;
-    const uint8_t* h = mc.host + b->off;
-    if (logits) *logits = (const float*)(h + b->out_lg) + r->row0 * d.n_classes;
-    if (step_masks) *step_masks = (const float*)(h + b->out_mk) + r->row0 * (int64_t)d.n_steps * d.d_emb;
-    if (agg_mask) *agg_mask = (const float*)(h + b->out_ag) + r->row0 * d.n_feat;
-    if (rows) *rows = r->rows;
-    return TABNET_OK;
-}
-
-int tabnet_server_release(tabnet_server* S, uint64_t ticket) {
-    if (!S) return tabnet::set_last_error(TABNET_ERR_ARG, "null server");
+    Request* r = nullptr;
+    const uint8_t* h = nullptr;
+    Batch* b = nullptr;
+    int slots = 0;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         auto it = S->reqs.find(ticket);
         if (it == S->reqs.end() || !it->second->batch || !it->second->batch->complete)
             return tabnet::set_last_error(TABNET_ERR_ARG, "ticket unknown, released or not complete");
-        it->second->batch->released++;
-        delete it->second;
-        S->reqs.erase(it);
+        r = it->second;
+        b = r->batch;
+        h = S->models[r->model].host + b->off;
+        slots = S->models[r->model].slots;
     }
-    S->cv.notify_all();
+    // the request's result memory stays put until the ticket is released
+    const tabnet_dims& d = S->models[r->model].d;
+    const int64_t S_de = (int64_t)d.n_steps * d.d_emb;
+    if (logits) *logits = (const float*)(h + b->out_lg) + r->row0 * d.n_classes;
+    if (agg_mask) *agg_mask = (const float*)(h + b->out_ag) + r->row0 * d.n_feat;
+    if (step_masks) {
+        if (b->dense) {
+            *step_masks = (const float*)(h + b->out_mk) + r->row0 * S_de;
+        } else {
+            if (r->dense_masks.empty()) {  // expand the compact form once
+                r->dense_masks.assign((size_t)(r->rows * S_de), 0.f);
+                const int64_t rs0 = r->row0 * d.n_steps, nrs = r->rows * d.n_steps;
+                const uint8_t* cnt = h + b->out_cnt + rs0;
+                const uint16_t* col = (const uint16_t*)(h + b->out_col) + rs0 * slots;
+                const float* val = (const float*)(h + b->out_val) + rs0 * slots;
+                for (int64_t i = 0; i < nrs; ++i) {
+                    float* dst = r->dense_masks.data() + i * d.d_emb;
+                    for (int j = 0; j < cnt[i]; ++j) dst[col[i * slots + j]] = val[i * slots + j];
+                }
+            }
+            *step_masks = r->dense_masks.data();
+        }
+    }
+    if (rows) *rows = r->rows;
     return TABNET_OK;
+}
+
+int tabnet_server_result_compact(tabnet_server* S, uint64_t ticket, const uint8_t** counts, const uint16_t** cols,
+                                 const float** vals, int* slots, int64_t* rows) {
+    if (!S || !counts || !cols || !vals || !slots) return tabnet::set_last_error(TABNET_ERR_ARG, "null pointer");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end() || !it->second->batch || !it->second->batch->complete)
+        return tabnet::set_last_error(TABNET_ERR_ARG, "ticket unknown, released or not complete");
+    const Request* r = it->second;
+    const Batch* b = r->batch;
+    const ModelCtx& mc = S->models[r->model];
+    if (rows) *rows = r->rows;
+    if (b->dense) {  // sent densely: read the masks through tabnet_server_result
+        *counts = nullptr;
+        *cols = nullptr;
+        *vals = nullptr;
+        *slots = 0;
+        return TABNET_OK;
+    }
+    const uint8_t* h = mc.host + b->off;
+    const int64_t rs0 = r->row0 * mc.d.n_steps;
+    *counts = h + b->out_cnt + rs0;
+    *cols = (const uint16_t*)(h + b->out_col) + rs0 * mc.slots;
+    *vals = (const float*)(h + b->out_val) + rs0 * mc.slots;
+    *slots = mc.slots;
+    return TABNET_OK;
+}
+
+namespace {
+// Release one ticket (the server lock held).
+int release_locked(tabnet_server* S, uint64_t ticket) {
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end() || !it->second->batch || !it->second->batch->complete)
+        return tabnet::set_last_error(TABNET_ERR_ARG, "ticket unknown, released or not complete");
+    it->second->batch->released++;
+    delete it->second;
+    S->reqs.erase(it);
+    return TABNET_OK;
+}
+
+// Release k tickets under one acquisition of the lock (the load driver's
+// path: one lock per ticket would contend with the engine at high rates).
+void release_group(tabnet_server* S, const uint64_t* tickets, int k) {
+    if (k <= 0) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (int j = 0; j < k; ++j) release_locked(S, tickets[j]);
+    }
+    if (S->engine_idle.load(std::memory_order_relaxed)) S->cv.notify_all();
+}
+}  // namespace
+
+int tabnet_server_release(tabnet_server* S, uint64_t ticket) {
+    if (!S) return tabnet::set_last_error(TABNET_ERR_ARG, "null server");
+    int rc;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        rc = release_locked(S, ticket);
+    }
+    if (rc == TABNET_OK && S->engine_idle.load(std::memory_order_relaxed)) S->cv.notify_all();
+    return rc;
 }
 
 int tabnet_server_wait(tabnet_server* S, uint64_t ticket, double timeout_s) {
@@ -471,7 +713,7 @@ int tabnet_server_get_stats(tabnet_server* S, tabnet_server_stats* st) {
         for (auto& mc : S->models) {
             q += (int64_t)mc.pending.size();
             inflight += (int64_t)mc.running;
-            used += mc.used;
+            used += mc.out.used + mc.in.used * mc.in_row;
         }
         st->queue_depth = q;
         st->inflight_batches = inflight;
@@ -514,7 +756,7 @@ int tabnet_server_replay(tabnet_server* S, const tabnet_server_request* reqs, in
                 last_poll = now;
                 int k = 0;
                 tabnet_server_poll(S, done.data(), (int)done.size(), &k);
-                for (int j = 0; j < k; ++j) tabnet_server_release(S, done[j]);
+                release_group(S, done.data(), k);
             }
         }
         uint64_t t;
@@ -525,7 +767,7 @@ int tabnet_server_replay(tabnet_server* S, const tabnet_server_request* reqs, in
         while (true) {
             int k = 0;
             const int rc = tabnet_server_poll(S, done.data(), (int)done.size(), &k);
-            for (int j = 0; j < k; ++j) tabnet_server_release(S, done[j]);
+            release_group(S, done.data(), k);
             if (rc != TABNET_OK) return rc;
             tabnet_server_stats st;
             tabnet_server_get_stats(S, &st);
@@ -556,6 +798,8 @@ void tabnet_server_destroy(tabnet_server* S) {
         for (Request* r : mc.pending) delete r;
         if (mc.dev) cudaFree(mc.dev);
         if (mc.host) cudaFreeHost(mc.host);
+        if (mc.in_dev) cudaFree(mc.in_dev);
+        if (mc.in_host) cudaFreeHost(mc.in_host);
     }
     for (cudaEvent_t e : S->free_events) cudaEventDestroy(e);
     for (auto& kv : S->reqs) {

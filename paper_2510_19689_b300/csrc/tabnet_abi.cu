@@ -263,7 +263,7 @@ int forward_impl(tabnet_model* m, const float* x_num, const int32_t* x_cat, int6
         p.seg = seg ? *seg : SegTable{nullptr, nullptr, 0};
         // a call of few rows (known on the host) takes a warp per row, with
         // results bit for bit those of the four-lanes-per-row kernel
-        if (!seg && rows <= m->simt_row_max)
+        if (!(seg && seg->segs) && rows <= m->simt_row_max)
             e = simt_row_launch(p, x_num, x_cat, rows, logits, masks, agg, stream, m->num_sms, kFp32RowWarpsMax,
                                 m->smem_optin);
         else
@@ -273,6 +273,27 @@ int forward_impl(tabnet_model* m, const float* x_num, const int32_t* x_cat, int6
     }
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return TABNET_OK;
+}
+
+// One batch whose input row i is n_num floats then n_cat int32 codes at
+// rows_in + 4 (n_num + n_cat) i (the server's input ring); outputs as in
+// tabnet_forward.  Not part of the C ABI.
+int forward_interleaved(tabnet_model* m, const void* rows_in, int64_t rows, float* logits, float* step_masks,
+                                float* agg_mask, cudaStream_t stream) {
+    if (!m || !rows_in) return fail(TABNET_ERR_ARG, "null model or inputs");
+    if (rows <= 0) return rows < 0 ? fail(TABNET_ERR_ARG, "rows < 0") : TABNET_OK;
+    const tabnet_dims& d = m->host.dims;
+    int rc;
+    if ((rc = check_ptr(rows_in, true, "rows_in")) || (rc = check_ptr(logits, true, "logits")) ||
+        (rc = check_ptr(step_masks, false, "step_masks")) || (rc = check_ptr(agg_mask, false, "agg_mask")))
+        return rc;
+    DeviceGuard guard(m->device);
+    if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+    SegTable t{nullptr, nullptr, 0};
+    t.in_stride = d.n_num + d.n_cat;
+    const float* xn = static_cast<const float*>(rows_in);
+    return forward_impl(m, d.n_num ? xn : nullptr, d.n_cat ? reinterpret_cast<const int32_t*>(xn + d.n_num) : nullptr,
+                        rows, logits, step_masks, agg_mask, stream, &t);
 }
 
 }  // namespace tabnet

@@ -1747,7 +1747,7 @@ cudaError_t tc_launch(tabnet_model* m, const float* x_num, const int* x_cat, int
     const TcLaunch& L = m->tc_launch_cfg;
     const int64_t slots = (int64_t)m->num_sms * L.ctas_per_sm;
     // a segmented launch learns its row count on the device: one CTA per slot
-    const unsigned grid = (unsigned)(seg ? slots : std::min<int64_t>((rows + 127) / 128, slots));
+    const unsigned grid = (unsigned)(seg && seg->segs ? slots : std::min<int64_t>((rows + 127) / 128, slots));
     const dim3 block(128 * L.nwg);
     const Variant v{p.m.N, L.nwg, precision_parts(m->precision), L.zreg, L.lean};
     const bool found = with_kernel(v, [&](auto fn) {

@@ -37,7 +37,7 @@ EXPORTS = (
     "tabnet_get_tile_config", "tabnet_forward_segments", "tabnet_forward_segments_device",
     "tabnet_reserve_segments", "tabnet_forward_segments_noalloc",
     "tabnet_server_create", "tabnet_server_submit", "tabnet_server_poll", "tabnet_server_wait",
-    "tabnet_server_result", "tabnet_server_release", "tabnet_server_get_stats", "tabnet_server_reset_stats",
+    "tabnet_server_result", "tabnet_server_result_compact", "tabnet_server_release", "tabnet_server_get_stats", "tabnet_server_reset_stats",
     "tabnet_server_replay", "tabnet_server_destroy", "tabnet_mask_stats", "tabnet_topk_agreement",
     "tabnet_set_input_transform",
 )
@@ -72,7 +72,7 @@ def segment_array(segs):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_size_t), ("max_batch_rows", ctypes.c_int),
                 ("max_inflight_batches", ctypes.c_int), ("streams_per_model", ctypes.c_int),
-                ("batch_min_rows", ctypes.c_int), ("batch_wait_us", ctypes.c_int)]
+                ("batch_min_rows", ctypes.c_int), ("batch_wait_us", ctypes.c_int), ("mask_slots", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -141,6 +141,9 @@ def lib() -> ctypes.CDLL:
     L.tabnet_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double]
     fpp = ctypes.POINTER(ctypes.POINTER(ctypes.c_float))
     L.tabnet_server_result.argtypes = [vp, ctypes.c_uint64, fpp, fpp, fpp, ctypes.POINTER(ctypes.c_int64)]
+    L.tabnet_server_result_compact.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.POINTER(ctypes.c_uint8)),
+                                               ctypes.POINTER(ctypes.POINTER(ctypes.c_uint16)), fpp,
+                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]
     L.tabnet_server_release.argtypes = [vp, ctypes.c_uint64]
     L.tabnet_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
     L.tabnet_server_reset_stats.argtypes = [vp]
@@ -305,11 +308,11 @@ class Server:
     (tabnet_server_*).  Inputs are numpy arrays kept alive until release."""
 
     def __init__(self, models, device_bytes=1 << 30, max_batch_rows=65536, max_inflight_batches=32,
-                 streams_per_model=8, batch_min_rows=512, batch_wait_us=200):
+                 streams_per_model=8, batch_min_rows=512, batch_wait_us=200, mask_slots=0):
         self.models = list(models)
         arr = (ctypes.c_void_p * len(self.models))(*[m.handle for m in self.models])
         cfg = ServerConfig(device_bytes, max_batch_rows, max_inflight_batches, streams_per_model, batch_min_rows,
-                           batch_wait_us)
+                           batch_wait_us, mask_slots)
         h = ctypes.c_void_p()
         _check(lib().tabnet_server_create(arr, len(self.models), ctypes.byref(cfg), ctypes.byref(h)),
                "tabnet_server_create")
@@ -343,6 +346,25 @@ class Server:
         mk = np.ctypeslib.as_array(pm, shape=(rows, d.n_steps, d.d_emb)).copy()
         ag = np.ctypeslib.as_array(pa, shape=(rows, d.n_feat)).copy()
         return lg, mk, ag
+
+    def result_compact(self, ticket: int):
+        """Copies of a completed request's compact step masks (counts
+        [rows, n_steps], cols and vals [rows, n_steps, slots]), or None when
+        its batch was sent densely."""
+        _, _, model, rows = self._keep[ticket]
+        d = self.models[model].dims
+        pc, pcol = ctypes.POINTER(ctypes.c_uint8)(), ctypes.POINTER(ctypes.c_uint16)()
+        pv = ctypes.POINTER(ctypes.c_float)()
+        slots, r = ctypes.c_int(), ctypes.c_int64()
+        _check(lib().tabnet_server_result_compact(self._h, ticket, ctypes.byref(pc), ctypes.byref(pcol),
+                                                  ctypes.byref(pv), ctypes.byref(slots), ctypes.byref(r)),
+               "tabnet_server_result_compact")
+        if slots.value == 0:
+            return None
+        k = slots.value
+        return (np.ctypeslib.as_array(pc, shape=(rows, d.n_steps)).copy(),
+                np.ctypeslib.as_array(pcol, shape=(rows, d.n_steps, k)).copy(),
+                np.ctypeslib.as_array(pv, shape=(rows, d.n_steps, k)).copy())
 
     def release(self, ticket: int) -> None:
         _check(lib().tabnet_server_release(self._h, ticket), "tabnet_server_release")

@@ -171,3 +171,41 @@ def test_same_result_under_the_default_policy(models):
     lg = alone[3][0]
     rl = O.forward(p6, xn, xc)[0]
     assert (np.abs(lg - rl) / np.maximum(np.abs(rl), 1)).max() <= 1e-5
+
+
+def test_mask_transfer_modes_are_exact(models):
+    """Step masks travel to the host compact (per row-step the nonzero
+    columns and their values) where that saves bytes; a batch with a row-step
+    over the slot count travels densely.  Compact (default slots), compact
+    overflowing into the dense fallback (one slot) and always dense must give
+    the same bits, equal to a direct forward of the same rows, and the
+    compact form must decode to those masks."""
+    tabnet, params, ms = models
+    reqs = [(i, *_req(n, r, 300 + 7 * i + r)) for i, n in enumerate(NAMES) for r in (1, 64, 257)]
+    direct = []
+    for i, xn, xc in reqs:
+        lg, mk, ag = ms[i].run(torch.from_numpy(xn).cuda(), torch.from_numpy(xc).cuda())
+        direct.append((lg.cpu().numpy(), mk.cpu().numpy(), ag.cpu().numpy()))
+    for slots in (0, 1, -1):
+        srv = tabnet.Server(ms, device_bytes=256 << 20, mask_slots=slots)
+        tickets = [srv.submit(i, xn, xc) for i, xn, xc in reqs]
+        for t, (i, xn, xc), ref in zip(tickets, reqs, direct):
+            srv.wait(t)
+            got = srv.result(t)
+            for a, b in zip(got, ref):
+                np.testing.assert_array_equal(a, b)
+            comp = srv.result_compact(t)
+            if slots == 0 and NAMES[i] in ("c2", "c3"):
+                assert comp is not None  # compact on the wide models, no overflow at these slot counts
+            if slots == -1 or (slots == 0 and NAMES[i] == "c1"):
+                assert comp is None      # dense by request, or the narrow model (no saving)
+            if comp is not None:
+                cnt, col, val = comp
+                mk = got[1]
+                np.testing.assert_array_equal(cnt, (mk != 0).sum(axis=2))
+                dec = np.zeros_like(mk)
+                for (r, s) in np.ndindex(cnt.shape):
+                    dec[r, s, col[r, s, :cnt[r, s]]] = val[r, s, :cnt[r, s]]
+                np.testing.assert_array_equal(dec, mk)
+            srv.release(t)
+        srv.close()
