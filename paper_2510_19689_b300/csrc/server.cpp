@@ -500,8 +500,12 @@ int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet
         const size_t share = (size_t)(S->cfg.device_bytes * (w[i] / wsum));
         const size_t ring_rows = share / (mc.in_row + mc.out_row);
         mc.out.cap = (ring_rows * mc.out_row + kRegionSlack) / 256 * 256;
-        mc.in.cap = ring_rows;
-        const size_t in_bytes = align256(ring_rows * mc.in_row);
+        // the input ring holds four times the output ring's rows (inputs are
+        // at most 400 bytes a row here, outputs up to 8.7 KB): a backlog
+        // waiting for output space must not fill it, or staging falls back
+        // onto the engine thread, whose time per request bounds the rate
+        mc.in.cap = 4 * ring_rows;
+        const size_t in_bytes = align256(mc.in.cap * mc.in_row);
         mc.stage_max = (int64_t)std::min(ring_rows, (mc.out.cap - kRegionSlack - 256) / mc.out_row);
         cudaError_t e1 = cudaMalloc(&mc.dev, mc.out.cap);
         cudaError_t e2 = cudaHostAlloc(&mc.host, mc.out.cap, cudaHostAllocDefault);
