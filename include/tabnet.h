@@ -60,7 +60,10 @@ extern "C" {
 /* Arithmetic of the fully connected layers.  In every mode the sparsemax
  * threshold, the prior, the masks and their aggregation are float32. */
 typedef enum {
-    TABNET_FP32 = 0,      /* float32 FMA everywhere (no TF32) */
+    TABNET_FP32 = 0,      /* float32 FMA everywhere (no TF32), on the CUDA cores;
+                             a call of at most 32 rows per SM runs one warp
+                             per row (the latency form), a larger one four
+                             lanes per row, with bit-identical results */
     TABNET_BF16 = 1,      /* bf16 x bf16 -> fp32 tensor-core FCs (tcgen05): every
                              BN-folded weight and every FC input rounded once
                              to bf16; the rest in fp32 */
