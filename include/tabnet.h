@@ -298,6 +298,8 @@ typedef struct {
     double rows_per_s;                               /* completed rows / time since reset */
     int64_t queue_depth, inflight_batches;
     size_t device_bytes_in_use;
+    uint64_t engine_staged;  /* requests whose inputs the engine copied (the input ring
+                                was full when they were submitted) */
 } tabnet_server_stats;
 
 /* One request of a replayed trace (tabnet_server_replay). */

@@ -143,6 +143,7 @@ struct tabnet_server {
     std::deque<uint64_t> completed;      // tickets completed, not yet returned by poll
     std::vector<double> lat_ms;          // completed requests' latencies since the last reset
     uint64_t submitted = 0, n_completed = 0, rejected = 0, rows_done = 0, batches = 0, batch_rows = 0;
+    uint64_t engine_staged = 0;
     Clock::time_point t_reset = Clock::now();
     std::thread engine;
     std::atomic<bool> stop{false};
@@ -342,6 +343,7 @@ void engine_loop(tabnet_server* S) {
                         if (!ring_alloc(mc.in, (size_t)r->rows, &row0)) break;  // admission waits for memory
                         r->in_row0 = (int64_t)row0;
                         --mc.unstaged;
+                        ++S->engine_staged;
                         stage_now.push_back(r);  // copied below, outside the lock
                     } else if (!r->ready.load(std::memory_order_acquire)) {
                         break;  // its submitter is still copying the inputs
@@ -722,6 +724,7 @@ int tabnet_server_get_stats(tabnet_server* S, tabnet_server_stats* st) {
         st->queue_depth = q;
         st->inflight_batches = inflight;
         st->device_bytes_in_use = used;
+        st->engine_staged = S->engine_staged;
         const double secs = std::chrono::duration<double>(Clock::now() - S->t_reset).count();
         st->rows_per_s = secs > 0 ? S->rows_done / secs : 0.0;
     }
@@ -741,7 +744,7 @@ int tabnet_server_reset_stats(tabnet_server* S) {
     if (!S) return tabnet::set_last_error(TABNET_ERR_ARG, "null server");
     std::lock_guard<std::mutex> lk(S->mu);
     S->lat_ms.clear();
-    S->submitted = S->n_completed = S->rejected = S->rows_done = S->batches = S->batch_rows = 0;
+    S->submitted = S->n_completed = S->rejected = S->rows_done = S->batches = S->batch_rows = S->engine_staged = 0;
     S->t_reset = Clock::now();
     return TABNET_OK;
 }

@@ -81,7 +81,8 @@ class ServerStats(ctypes.Structure):
                 ("mean_batch_rows", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p95_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("rows_per_s", ctypes.c_double), ("queue_depth", ctypes.c_int64),
-                ("inflight_batches", ctypes.c_int64), ("device_bytes_in_use", ctypes.c_size_t)]
+                ("inflight_batches", ctypes.c_int64), ("device_bytes_in_use", ctypes.c_size_t),
+                ("engine_staged", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

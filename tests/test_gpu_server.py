@@ -81,19 +81,30 @@ def test_same_result_alone_and_in_a_mix(models):
 
 
 def test_admission_waits_for_memory(models):
+    """Rings sized for a few hundred rows of the 100-input model: requests
+    submitted faster than they complete find its input ring full, queue
+    unstaged and are copied in by the engine later, in order -- and still
+    give the same bits as a direct forward of their rows."""
     tabnet, params, ms = models
-    # rings sized for only a few hundred rows of the 100-input model
     srv = tabnet.Server(ms, device_bytes=8 << 20, max_batch_rows=512)
-    tickets = []
+    tickets, reqs = [], []
     for k in range(60):
         i = k % 3
         xn, xc = _req(NAMES[i], 200, 2000 + k)
+        reqs.append((i, xn, xc))
         tickets.append(srv.submit(i, xn, xc))
+    results = []
     for t in tickets:
         srv.wait(t, 60.0)
+        results.append(srv.result(t))
         srv.release(t)
     st = srv.stats()
     assert st["completed"] == 60 and st["rejected"] == 0
+    assert st["engine_staged"] > 0  # the full-ring path ran
+    for (i, xn, xc), got in zip(reqs, results):
+        ref = ms[i].run(torch.from_numpy(xn).cuda(), torch.from_numpy(xc).cuda())
+        for a, b in zip(got, ref):
+            np.testing.assert_array_equal(a, b.cpu().numpy())
     # a request larger than its model's whole ring is rejected, not hung
     xn, xc = _req("c3", 4000, 3000)
     srv.submit(2, xn, xc)
