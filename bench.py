@@ -371,7 +371,8 @@ def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), s
         out.append({"offered_req_per_s": rate, "requests": n, "completed": st["completed"],
                     "achieved_req_per_s": st["completed"] / wall, "rows_per_s": st["rows_completed"] / wall,
                     "p50_ms": st["p50_ms"], "p95_ms": st["p95_ms"], "p99_ms": st["p99_ms"],
-                    "mean_batch_rows": st["mean_batch_rows"], "batches": st["batches"]})
+                    "mean_batch_rows": st["mean_batch_rows"], "batches": st["batches"],
+                    "engine_staged": st["engine_staged"]})
     srv.close()
     for m in models:
         m.close()

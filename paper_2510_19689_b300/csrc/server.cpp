@@ -117,7 +117,9 @@ struct ModelCtx {
     Ring in;
     int slots = 0;                 // compact mask slots per (row, step); 0: dense transfer
     int64_t stage_max = 0;         // rows a request may have to be staged (fits both rings)
-    int64_t unstaged = 0;          // queued requests whose inputs are not in the input ring yet
+    // queued requests whose inputs are not in the input ring yet, in
+    // submission order (all of them after every staged request)
+    std::deque<Request*> unstaged;
     std::deque<Batch*> in_order;   // batches holding input rows, in ring order
     std::deque<Batch*> inflight;   // in output-ring order
     std::deque<Request*> pending;
@@ -333,7 +335,7 @@ void engine_loop(tabnet_server* S) {
                             // could never fit: reject
                             mc.pending.pop_front();
                             mc.pending_rows -= r->rows;
-                            --mc.unstaged;
+                            mc.unstaged.pop_front();  // r: the oldest unstaged request
                             S->reqs.erase(r->ticket);
                             ++S->rejected;
                             delete r;
@@ -342,7 +344,7 @@ void engine_loop(tabnet_server* S) {
                         size_t row0 = 0;
                         if (!ring_alloc(mc.in, (size_t)r->rows, &row0)) break;  // admission waits for memory
                         r->in_row0 = (int64_t)row0;
-                        --mc.unstaged;
+                        mc.unstaged.pop_front();
                         ++S->engine_staged;
                         stage_now.push_back(r);  // copied below, outside the lock
                     } else if (!r->ready.load(std::memory_order_acquire)) {
@@ -541,28 +543,36 @@ int tabnet_server_submit(tabnet_server* S, int model, const float* x_num, const 
     r->rows = rows;
     r->t_submit = Clock::now();
     r->ticket = S->next_ticket.fetch_add(1);
-    bool staged = false;
     ModelCtx& mc = S->models[model];
+    // requests this call copies in: older ones still waiting for room in the
+    // input ring first (in order), then this one
+    Request* to_stage[8];
+    int n_stage = 0;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         S->reqs.emplace(r->ticket, r);
-        // the inputs go to the input ring now, in submission order, unless
-        // an older request is still waiting for room there (then the engine
-        // copies this one later, in order)
-        size_t row0 = 0;
-        if (mc.unstaged == 0 && rows <= mc.stage_max && ring_alloc(mc.in, (size_t)rows, &row0)) {
-            r->in_row0 = (int64_t)row0;
-            staged = true;
-        } else {
-            ++mc.unstaged;
+        mc.unstaged.push_back(r);
+        // The inputs go to the input ring in submission order.  A request
+        // that finds it full waits, unstaged; later submissions take over
+        // the oldest waiting ones as room frees (a few per call), so that a
+        // backlog's copies do not fall to the engine thread, whose time per
+        // request bounds the rate (the engine copies one only when it comes
+        // to the front of a batch with nobody having taken it).
+        while (!mc.unstaged.empty() && n_stage < 8) {
+            Request* u = mc.unstaged.front();
+            size_t row0 = 0;
+            if (u->rows > mc.stage_max || !ring_alloc(mc.in, (size_t)u->rows, &row0)) break;
+            u->in_row0 = (int64_t)row0;
+            mc.unstaged.pop_front();
+            to_stage[n_stage++] = u;
         }
         mc.pending.push_back(r);
         mc.pending_rows += rows;
         ++S->submitted;
     }
-    // the copy runs on the submitting thread, outside the lock; the engine
-    // takes the request into a batch once it is marked ready
-    if (staged) stage_inputs(mc, r);
+    // the copies run on the submitting thread, outside the lock; the engine
+    // takes a request into a batch once it is marked ready
+    for (int i = 0; i < n_stage; ++i) stage_inputs(mc, to_stage[i]);
     // a wake-up only when the engine sleeps (a missed one costs at most its
     // 50 us nap): a notify is a system call, and submit runs per request
     if (S->engine_idle.load(std::memory_order_relaxed)) S->cv.notify_all();
