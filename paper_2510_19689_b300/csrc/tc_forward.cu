@@ -31,7 +31,9 @@
 //     row: 64 bf16 or 128 e4m3 elements) per slot, pre-swizzled by the host;
 //     a K block's parts sit in consecutive slots and arrive by one copy (a
 //     copy costs the issuing thread a few hundred cycles when every SM is
-//     copying).  Thread 0 issues copies and MMAs; each such unit has a
+//     copying).  Warp 0 keeps the ring's bookkeeping in every lane (warp-
+//     uniform descriptors and loop state) and its lane 0 issues copies and
+//     MMAs; each such unit has a
 //     "full" barrier (copy landed); a unit read by a layer's last K block is
 //     free once the accumulator barrier fires, earlier blocks' units get
 //     their own "empty" commit.
@@ -313,7 +315,7 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     // barrier.
     const int SU = S / PARTS;
     const int64_t total_chunks = my_tiles * p.chunks_per_tile;
-    // Ring bookkeeping (thread 0 only), incremental so that no 64-bit
+    // Ring bookkeeping (every lane of warp 0), incremental so that no 64-bit
     // division sits on the MMA critical path: unit g of the CTA's stream
     // goes to ring unit g mod SU in round g / SU, and is unit g mod
     // chunks_per_tile of a tile's sequence.
@@ -330,30 +332,41 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     int xc = 0;
     int lc = 0;  // layers run by this CTA
 
-    // Thread 0: start the copy of unit g_issue once its ring unit is free
-    // (the MMAs that read its previous occupant have completed).
+    // Warp 0 drives the ring and the MMAs: every lane runs the bookkeeping
+    // (so the descriptors and loop state are warp-uniform) and lane 0 issues
+    // the copies, MMAs and commits.  A wait's outcome is lane 0's.
+    const int lane_id = tid & 31;
+    auto warp_wait = [&](uint32_t bar, uint32_t parity) -> bool {
+        const bool w = ptx::mbar_wait(bar, parity, kWaitLimit);
+        return __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
+    };
+    // Start the copy of unit g_issue once its ring unit is free (the MMAs
+    // that read its previous occupant have completed).
     auto issue_next = [&]() -> bool {
         const int slot = is_slot;
         if (empty_pending & (1u << slot)) {
-            if (!ptx::mbar_wait(bar_empty + 8 * slot, (empty_par >> slot) & 1u, kWaitLimit)) {
-                note_timeout(m.status, 5, (unsigned)g_issue);
+            if (!warp_wait(bar_empty + 8 * slot, (empty_par >> slot) & 1u)) {
+                if (lane_id == 0) note_timeout(m.status, 5, (unsigned)g_issue);
                 return false;
             }
             empty_par ^= 1u << slot;
             empty_pending &= ~(1u << slot);
         }
         const uint2 ck = sChunks[is_chunk];
-        ptx::mbar_arrive_expect_tx(bar_full + 8 * slot, ck.y);
-        ptx::bulk_g2s(ring_base + (uint32_t)(slot * PARTS * p.slot_bytes), p.wbase + ck.x, ck.y, bar_full + 8 * slot);
+        if (lane_id == 0) {
+            ptx::mbar_arrive_expect_tx(bar_full + 8 * slot, ck.y);
+            ptx::bulk_g2s(ring_base + (uint32_t)(slot * PARTS * p.slot_bytes), p.wbase + ck.x, ck.y,
+                          bar_full + 8 * slot);
+        }
         ++g_issue;
         if (++is_chunk == p.chunks_per_tile) is_chunk = 0;
         if (++is_slot == SU) is_slot = 0;
         return true;
     };
-    if (tid == 0)
+    if (warp == 0)
         while (g_issue < total_chunks && g_issue < SU) issue_next();
 
-    // Publish this thread's A-operand writes and TMEM reads, then let thread 0
+    // Publish this thread's A-operand writes and TMEM reads, then let warp 0
     // run one layer's MMA chain (K steps of 16 columns [kbeg, kend) over the
     // 64-wide K blocks that hold them) and wait for the accumulator.
     // Returns false when the CTA has to stop.
@@ -364,15 +377,15 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         ptx::tc_fence_before();
         __syncthreads();
         if (sAbort[lc & 1]) return false;
-        if (tid == 0) {
+        if (warp == 0) {
             ptx::tc_fence_after();
             bool ok = true;
 #pragma unroll 1
             for (int b = kbeg >> 2; 4 * b < kend && ok; ++b) {
                 while (ok && g_issue < g_cons + 1) ok = issue_next();
                 // this K block's unit: its parts in consecutive slots
-                if (ok && !ptx::mbar_wait(bar_full + 8 * cs_slot, cs_round & 1u, kWaitLimit)) {
-                    note_timeout(m.status, 1, (unsigned)g_cons);
+                if (ok && !warp_wait(bar_full + 8 * cs_slot, cs_round & 1u)) {
+                    if (lane_id == 0) note_timeout(m.status, 1, (unsigned)g_cons);
                     ok = false;
                 }
                 if (!ok) break;
@@ -385,60 +398,60 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     d_a[part] = ptx::sw128_desc(a_base + (uint32_t)part * a_part + (uint32_t)(b * 16384));
                 }
                 const int k0 = max(kbeg - 4 * b, 0), k1 = min(kend - 4 * b, 4);
-                if constexpr (NP == 3) {
-                    // Products whose parts' significance reaches 2^-16 of hi hi:
-                    // the five small ones first, so that most additions into
-                    // the accumulator happen while it is still small (each
-                    // rounds relative to the running sum), then hi hi.
+                if (lane_id == 0) {  // the block's MMAs, then release its unit if more blocks follow
+                    if constexpr (NP == 3) {
+                        // Products whose parts' significance reaches 2^-16 of hi hi:
+                        // the five small ones first, so that most additions into
+                        // the accumulator happen while it is still small (each
+                        // rounds relative to the running sum), then hi hi.
 #pragma unroll
-                    for (int k4 = 0; k4 < 4; ++k4) {
-                        if (k4 >= k0 && k4 < k1) {
-                            const uint64_t step = 2u * (uint32_t)k4;
-                            ptx::mma_f16(tmem, d_a[0] + step, d_b[1] + step, idesc, (4 * b + k4) > kbeg ? 1u : 0u);
-                            ptx::mma_f16(tmem, d_a[1] + step, d_b[0] + step, idesc, 1u);
-                            ptx::mma_f16(tmem, d_a[0] + step, d_b[2] + step, idesc, 1u);
-                            ptx::mma_f16(tmem, d_a[1] + step, d_b[1] + step, idesc, 1u);
-                            ptx::mma_f16(tmem, d_a[2] + step, d_b[0] + step, idesc, 1u);
-                        }
-                    }
-#pragma unroll
-                    for (int k4 = 0; k4 < 4; ++k4) {
-                        if (k4 >= k0 && k4 < k1) {
-                            const uint64_t step = 2u * (uint32_t)k4;
-                            ptx::mma_f16(tmem, d_a[0] + step, d_b[0] + step, idesc, 1u);
-                        }
-                    }
-                } else if constexpr (FP8) {
-                    // 32 e4m3 elements (32 bytes) per K step
-#pragma unroll
-                    for (int k4 = 0; k4 < 4; ++k4) {
-                        if (k4 >= k0 && k4 < k1) {
-                            const uint64_t step = 2u * (uint32_t)k4;
-                            ptx::mma_f8(tmem, d_a[0] + step, d_b[0] + step, idesc, (4 * b + k4) > kbeg ? 1u : 0u);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int k4 = 0; k4 < 4; ++k4) {
-                        if (k4 >= k0 && k4 < k1) {
-                            // hi hi; with two parts also hi lo and lo hi
-                            const uint64_t step = 2u * (uint32_t)k4;
-                            ptx::mma_f16(tmem, d_a[0] + step, d_b[0] + step, idesc, (4 * b + k4) > kbeg ? 1u : 0u);
-                            if constexpr (NP >= 2) {
-                                ptx::mma_f16(tmem, d_a[0] + step, d_b[1] + step, idesc, 1u);
+                        for (int k4 = 0; k4 < 4; ++k4) {
+                            if (k4 >= k0 && k4 < k1) {
+                                const uint64_t step = 2u * (uint32_t)k4;
+                                ptx::mma_f16(tmem, d_a[0] + step, d_b[1] + step, idesc, (4 * b + k4) > kbeg ? 1u : 0u);
                                 ptx::mma_f16(tmem, d_a[1] + step, d_b[0] + step, idesc, 1u);
+                                ptx::mma_f16(tmem, d_a[0] + step, d_b[2] + step, idesc, 1u);
+                                ptx::mma_f16(tmem, d_a[1] + step, d_b[1] + step, idesc, 1u);
+                                ptx::mma_f16(tmem, d_a[2] + step, d_b[0] + step, idesc, 1u);
+                            }
+                        }
+#pragma unroll
+                        for (int k4 = 0; k4 < 4; ++k4) {
+                            if (k4 >= k0 && k4 < k1) {
+                                const uint64_t step = 2u * (uint32_t)k4;
+                                ptx::mma_f16(tmem, d_a[0] + step, d_b[0] + step, idesc, 1u);
+                            }
+                        }
+                    } else if constexpr (FP8) {
+                        // 32 e4m3 elements (32 bytes) per K step
+#pragma unroll
+                        for (int k4 = 0; k4 < 4; ++k4) {
+                            if (k4 >= k0 && k4 < k1) {
+                                const uint64_t step = 2u * (uint32_t)k4;
+                                ptx::mma_f8(tmem, d_a[0] + step, d_b[0] + step, idesc, (4 * b + k4) > kbeg ? 1u : 0u);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int k4 = 0; k4 < 4; ++k4) {
+                            if (k4 >= k0 && k4 < k1) {
+                                // hi hi; with two parts also hi lo and lo hi
+                                const uint64_t step = 2u * (uint32_t)k4;
+                                ptx::mma_f16(tmem, d_a[0] + step, d_b[0] + step, idesc, (4 * b + k4) > kbeg ? 1u : 0u);
+                                if constexpr (NP >= 2) {
+                                    ptx::mma_f16(tmem, d_a[0] + step, d_b[1] + step, idesc, 1u);
+                                    ptx::mma_f16(tmem, d_a[1] + step, d_b[0] + step, idesc, 1u);
+                                }
                             }
                         }
                     }
+                    if (4 * (b + 1) < kend) ptx::mma_commit(bar_empty + 8 * cs_slot);
                 }
-                if (4 * (b + 1) < kend) {
-                    ptx::mma_commit(bar_empty + 8 * cs_slot);
-                    empty_pending |= 1u << cs_slot;
-                }
+                if (4 * (b + 1) < kend) empty_pending |= 1u << cs_slot;
                 g_cons += 1;
                 if (++cs_slot == SU) { cs_slot = 0; ++cs_round; }
             }
-            ptx::mma_commit(bar_acc);
+            if (lane_id == 0) ptx::mma_commit(bar_acc);
             acc_outstanding = true;
             if (!ok) sAbort[(lc + 1) & 1] = 1;
         }
@@ -446,24 +459,23 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
         // With two warpgroups every thread waits for the accumulator itself,
         // suspended in the barrier's try-wait (no issue slots spent), so each
         // warp's epilogue starts as soon as the MMAs complete rather than
-        // after thread 0 has woken, refilled the ring and released a 256-thread
-        // barrier (+2 % on the 100-input model).  With one warpgroup thread 0
+        // after warp 0 has woken, refilled the ring and released a 256-thread
+        // barrier (+2 % on the 100-input model).  With one warpgroup warp 0
         // waits alone and the others park on the CTA barrier (the all-thread
         // wait measured 1 % slower there).  No thread can fall a phase behind:
         // the next commit needs every thread at the next layer's CTA barrier.
         constexpr bool kAllWait = NWG == 2;
         bool got = true;
-        if (kAllWait || tid == 0) {
-            got = ptx::mbar_wait(bar_acc, acc_phase, kWaitLimit);
-            if (!got) {
-                sAbort[(lc + 1) & 1] = 1;
-                note_timeout(m.status, 2, (unsigned)lc);
-            }
+        if (warp == 0) got = warp_wait(bar_acc, acc_phase);
+        else if (kAllWait) got = ptx::mbar_wait(bar_acc, acc_phase, kWaitLimit);
+        if (!got) {
+            sAbort[(lc + 1) & 1] = 1;
+            if (warp != 0 || lane_id == 0) note_timeout(m.status, 2, (unsigned)lc);
         }
-        if (tid == 0) {
+        if (warp == 0) {
             if (got) acc_outstanding = false;
             // every MMA so far has completed: refill the free slots
-            if (!sAbort[(lc + 1) & 1])
+            if (__shfl_sync(0xffffffffu, sAbort[(lc + 1) & 1], 0) == 0)
                 while (g_issue < total_chunks && g_issue < g_cons + SU)
                     if (!issue_next()) { sAbort[(lc + 1) & 1] = 1; break; }
         }
@@ -1220,18 +1232,18 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
 
     // ---- teardown: no copy or MMA may still target this CTA's memory
     __syncthreads();
-    if (tid == 0) {
+    if (warp == 0) {
         int sl = cs_slot;
         uint32_t rd = cs_round;
         for (int64_t g = g_cons; g < g_issue; ++g) {
-            if (!ptx::mbar_wait(bar_full + 8 * sl, rd & 1u, kWaitLimit)) note_timeout(m.status, 3, (unsigned)g);
+            if (!warp_wait(bar_full + 8 * sl, rd & 1u) && lane_id == 0) note_timeout(m.status, 3, (unsigned)g);
             if (++sl == SU) { sl = 0; ++rd; }
         }
-        if (acc_outstanding && !ptx::mbar_wait(bar_acc, acc_phase ^ 1, kWaitLimit))
+        if (acc_outstanding && !warp_wait(bar_acc, acc_phase ^ 1) && lane_id == 0)
             note_timeout(m.status, 4, (unsigned)lc);
         for (int sl2 = 0; sl2 < SU; ++sl2)
             if ((empty_pending >> sl2) & 1u)
-                if (!ptx::mbar_wait(bar_empty + 8 * sl2, (empty_par >> sl2) & 1u, kWaitLimit))
+                if (!warp_wait(bar_empty + 8 * sl2, (empty_par >> sl2) & 1u) && lane_id == 0)
                     note_timeout(m.status, 6, (unsigned)sl2);
     }
     ptx::tc_fence_before();
