@@ -340,11 +340,13 @@ def fp8_gemm_peak(dev, n=8192, reps=10):
 
 
 def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), seconds=1.0,
-                  streams_per_model=16, max_inflight_batches=32):
+                  streams_per_model=16, max_inflight_batches=32, batch_min_rows=2048, batch_wait_us=200,
+                  clients=4, batch_busy=2):
     """Poisson arrivals at each rate for `seconds`, request sizes
     floor(exp(U(0, ln 513))) in [1, 512] rows, the three model shapes
-    resident (split-bf16), model chosen uniformly; the server's latency
-    (completion seen on the host - submission) and completed rows/s."""
+    resident (split-bf16), model chosen uniformly, submitted by `clients`
+    threads; the server's latency (completion seen on the host - scheduled
+    arrival, so a late submission counts) and completed rows/s."""
     import numpy as np
     from paper_2510_19689_b300 import synth, tabnet
     names = ["c1", "c2", "c3"]
@@ -352,7 +354,8 @@ def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), s
                            device=dev_index) for n in names]
     pools = [synth.make_rows(n, 512, seed=5000 + i) for i, n in enumerate(names)]
     srv = tabnet.Server(models, device_bytes=2 << 30, streams_per_model=streams_per_model,
-                        max_inflight_batches=max_inflight_batches)
+                        max_inflight_batches=max_inflight_batches, batch_min_rows=batch_min_rows,
+                        batch_wait_us=batch_wait_us, batch_busy=batch_busy)
     out = []
     for rate in rates:
         rng = np.random.default_rng(rate)
@@ -365,20 +368,24 @@ def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), s
         prepared = srv.prepare_replay(reqs)  # marshalling stays outside the timed region
         srv.reset_stats()
         t0 = time.perf_counter()
-        srv.replay_prepared(prepared)
+        srv.replay_prepared(prepared, threads=clients)
         wall = time.perf_counter() - t0
         st = srv.stats()
         out.append({"offered_req_per_s": rate, "requests": n, "completed": st["completed"],
                     "achieved_req_per_s": st["completed"] / wall, "rows_per_s": st["rows_completed"] / wall,
                     "p50_ms": st["p50_ms"], "p95_ms": st["p95_ms"], "p99_ms": st["p99_ms"],
                     "mean_batch_rows": st["mean_batch_rows"], "batches": st["batches"],
-                    "engine_staged": st["engine_staged"]})
+                    "engine_staged": st["engine_staged"], "p50_queue_ms": st["p50_queue_ms"],
+                    "p99_queue_ms": st["p99_queue_ms"], "engine_busy": st["engine_busy"],
+                    "engine_max_pass_ms": st["engine_max_pass_ms"], "replay_max_late_ms": st["replay_max_late_ms"],
+                    "p50_from_submit_ms": st["p50_submit_ms"], "p99_from_submit_ms": st["p99_submit_ms"]})
     srv.close()
     for m in models:
         m.close()
     return {"models": "14-, 35- and 100-input models resident, split-bf16", "request_rows": "log-uniform 1..512",
+            "clients": clients, "latency": "completion seen on the host - scheduled arrival",
             "server": {"streams_per_model": streams_per_model, "max_inflight_batches": max_inflight_batches,
-                       "batch_min_rows": 512, "batch_wait_us": 200,
+                       "batch_min_rows": batch_min_rows, "batch_wait_us": batch_wait_us, "batch_busy": batch_busy,
                        "step_masks": "compact (count + column/value slots) for the 35- and 100-input models, "
                                      "dense for the 14-input one"},
             "rates": out}

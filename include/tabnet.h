@@ -280,10 +280,13 @@ typedef struct {
                                   but unreleased results hold ring memory, not a slot */
     int streams_per_model;     /* CUDA streams per model (0: 8, at most 64): small batches of
                                   one model run side by side on different SMs */
-    int batch_min_rows;        /* adaptive batching: once half of a model's streams are busy, a
-                                  batch of fewer rows than this (0: 512; < 0: off) waits ... */
+    int batch_min_rows;        /* adaptive batching: once batch_busy of a model's batches are
+                                  running, a batch of fewer rows than this (0: 2048; < 0: off)
+                                  waits ... */
     int batch_wait_us;         /* ... for more requests, at most this long for its oldest
                                   (0: 200 us), so that one launch serves more rows under load */
+    int batch_busy;            /* adaptive batching engages once this many of a model's batches are
+                                  running (0: 2) */
     int mask_slots;            /* step masks go to the host compact: per (row, step) the count of
                                   nonzero columns and up to this many (column, value) pairs,
                                   exact; a batch with a row-step over the limit is sent densely.
@@ -294,12 +297,21 @@ typedef struct {
 typedef struct {
     uint64_t submitted, completed, rejected, rows_completed, batches;
     double mean_batch_rows;
-    double p50_ms, p95_ms, p99_ms, mean_ms, max_ms;  /* latency of completed requests */
+    double p50_ms, p95_ms, p99_ms, mean_ms, max_ms;  /* latency of completed requests: completion seen
+                                                        on the host - arrival (submission, or a replayed
+                                                        request's scheduled arrival) */
     double rows_per_s;                               /* completed rows / time since reset */
     int64_t queue_depth, inflight_batches;
     size_t device_bytes_in_use;
     uint64_t engine_staged;  /* requests whose inputs the engine copied (the input ring
                                 was full when they were submitted) */
+    double p50_queue_ms, p99_queue_ms;  /* of completed requests: submission -> their batch's launch */
+    double engine_busy;      /* fraction of the time since the reset the engine thread was not
+                                asleep waiting for work */
+    double engine_max_pass_ms;  /* longest single engine pass (completions + launches) */
+    double replay_max_late_ms;  /* tabnet_server_replay: latest submission behind its arrival */
+    double p50_submit_ms, p99_submit_ms;  /* latency counted from the submission call instead (the
+                                             server's share when a replay client fell behind) */
 } tabnet_server_stats;
 
 /* One request of a replayed trace (tabnet_server_replay). */
@@ -365,10 +377,15 @@ int tabnet_server_get_stats(tabnet_server* server, tabnet_server_stats* stats);
 int tabnet_server_reset_stats(tabnet_server* server);
 
 /* Load driver: submit reqs[i] at its arrival offset (busy-waiting on the
- * host clock) from the calling thread; with `release` != 0 completed
- * requests are released as they finish and the call returns when all are
- * done.  Errors: as tabnet_server_submit. */
-int tabnet_server_replay(tabnet_server* server, const tabnet_server_request* reqs, int n, int release);
+ * host clock) from `threads` submitting threads (<= 0: 1, at most 64;
+ * thread j takes requests j, j + threads, ... in order), standing for that
+ * many clients; a replayed request's latency counts from its scheduled
+ * arrival, so a submission that comes late counts too.  With `release` != 0
+ * completed requests are released as they finish (polled every 20 us,
+ * between submissions too when a thread is behind schedule) and the call
+ * returns when all are done.  Errors: as tabnet_server_submit. */
+int tabnet_server_replay(tabnet_server* server, const tabnet_server_request* reqs, int n, int release,
+                         int threads);
 
 /* Stop the engine, wait for the GPU, free everything. */
 void tabnet_server_destroy(tabnet_server* server);

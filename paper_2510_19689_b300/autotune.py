@@ -37,7 +37,7 @@ def candidates(model: "tabnet.Model"):
     nwgs = [2] if n == 128 else ([1] if n == 16 else [1, 2])
     for nwg in nwgs:
         for cps in (1, 2, 3, 4):
-            for slots in (2, 3, 4, 6, 8):
+            for slots in (1, 2, 3, 4, 6, 8):
                 yield dict(nwg=nwg, n_slots=slots, ctas_per_sm=cps)
 
 

@@ -64,7 +64,10 @@ struct Request {
     const float* x_num = nullptr;
     const int32_t* x_cat = nullptr;
     int64_t rows = 0;
-    Clock::time_point t_submit;
+    // arrival: the submission time, or a replayed request's scheduled
+    // arrival (a late submission then counts in its latency)
+    Clock::time_point t_arrival;
+    Clock::time_point t_submit;  // when the submission call ran
     // rows of the model's input ring holding the inputs (-1: not staged
     // yet), and whether they are copied there
     int64_t in_row0 = -1;
@@ -126,6 +129,10 @@ struct ModelCtx {
     std::vector<cudaStream_t> streams;
     int next_stream = 0;
     int running = 0;               // batches launched and not yet complete
+    // running estimate of a batch's time from launch to its completion being
+    // seen (us; 0 until the first): a batch is not asked before most of it
+    // has passed, so the engine's event queries stay few per batch
+    double est_us = 0;
     int64_t pending_rows = 0;      // rows of the pending requests
 };
 
@@ -144,6 +151,11 @@ struct tabnet_server {
     std::atomic<uint64_t> next_ticket{1};
     std::deque<uint64_t> completed;      // tickets completed, not yet returned by poll
     std::vector<double> lat_ms;          // completed requests' latencies since the last reset
+    std::vector<double> queue_ms;        // their arrival -> batch launch times
+    std::vector<double> sub_ms;          // their submission call -> completion times
+    double engine_sleep_s = 0;           // engine time asleep on cv since the last reset
+    double engine_max_pass_ms = 0;       // longest engine pass (completions + launches) since the reset
+    std::atomic<int64_t> replay_max_late_ns{0};  // latest replayed submission behind its arrival
     uint64_t submitted = 0, n_completed = 0, rejected = 0, rows_done = 0, batches = 0, batch_rows = 0;
     uint64_t engine_staged = 0;
     Clock::time_point t_reset = Clock::now();
@@ -222,6 +234,7 @@ void engine_loop(tabnet_server* S) {
     std::vector<Request*> take, stage_now;
     while (!S->stop.load(std::memory_order_relaxed)) {
         bool did = false;
+        const auto t_pass = Clock::now();
         // 1. completions: batches of one stream finish in order, batches of
         // different streams in any order, so each stream's oldest unfinished
         // batch is asked and a stream is skipped once one of its batches is
@@ -234,9 +247,11 @@ void engine_loop(tabnet_server* S) {
                 if (b->complete) continue;
                 const uint64_t bit = 1ull << (b->stream_idx & 63);
                 if (blocked & bit) continue;
-                // no batch completes within 20 us of its launch (copies and
-                // one kernel), and one found running is asked again 10 us
-                // later: a query costs the engine about a microsecond
+                // a batch is first asked once 3/4 of the model's recent
+                // launch-to-completion time (at least 20 us) has passed, and
+                // one found running is asked again 10 us later: a query costs
+                // the engine about a microsecond, and asking every running
+                // batch of three models every 10 us took most of its time
                 if (t_now < b->next_query) {
                     blocked |= bit;
                     continue;
@@ -246,6 +261,10 @@ void engine_loop(tabnet_server* S) {
                     b->next_query = t_now + std::chrono::microseconds(10);
                     blocked |= bit;
                     continue;
+                }
+                if (q == cudaSuccess && !b->dense_pending) {
+                    const double obs = std::chrono::duration<double, std::micro>(t_now - b->t_launch).count();
+                    mc.est_us = mc.est_us > 0 ? 0.9 * mc.est_us + 0.1 * obs : obs;
                 }
                 if (q == cudaSuccess && !b->dense) {
                     if (b->dense_pending) {
@@ -278,7 +297,10 @@ void engine_loop(tabnet_server* S) {
                 for (uint64_t t : b->tickets) {
                     auto it = S->reqs.find(t);
                     if (it == S->reqs.end()) continue;
-                    S->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - it->second->t_submit).count());
+                    S->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - it->second->t_arrival).count());
+                    S->sub_ms.push_back(std::chrono::duration<double, std::milli>(now - it->second->t_submit).count());
+                    S->queue_ms.push_back(
+                        std::chrono::duration<double, std::milli>(b->t_launch - it->second->t_arrival).count());
                     S->completed.push_back(t);
                     S->rows_done += it->second->rows;
                     ++S->n_completed;
@@ -318,12 +340,13 @@ void engine_loop(tabnet_server* S) {
                 std::lock_guard<std::mutex> lk(S->mu);
                 // only batches still on the GPU count; finished results hold ring memory instead
                 if (mc.pending.empty() || mc.running >= S->cfg.max_inflight_batches) continue;
-                // Under load (half the model's streams busy) a small batch waits
-                // for more requests -- up to batch_wait_us for its oldest -- so
-                // that the engine's fixed cost per launch is shared by more rows.
-                if (S->cfg.batch_min_rows > 0 && mc.running >= std::max(2, S->cfg.streams_per_model / 2) &&
+                // Under load (batch_busy of the model's batches running) a small
+                // batch waits for more requests -- up to batch_wait_us for its
+                // oldest -- so that the engine's fixed cost per launch is shared
+                // by more rows.
+                if (S->cfg.batch_min_rows > 0 && mc.running >= S->cfg.batch_busy &&
                     mc.pending_rows < S->cfg.batch_min_rows &&
-                    Clock::now() - mc.pending.front()->t_submit < std::chrono::microseconds(S->cfg.batch_wait_us))
+                    Clock::now() - mc.pending.front()->t_arrival < std::chrono::microseconds(S->cfg.batch_wait_us))
                     continue;
                 int64_t next_row = -1;  // the input row the batch continues at
                 while (!mc.pending.empty()) {
@@ -413,7 +436,7 @@ void engine_loop(tabnet_server* S) {
             cudaMemcpyAsync(mc.host + off, dv, b->copy_bytes, cudaMemcpyDeviceToHost, st);
             cudaEventRecord(b->done, st);
             b->t_launch = Clock::now();
-            b->next_query = b->t_launch + std::chrono::microseconds(20);
+            b->next_query = b->t_launch + std::chrono::microseconds(std::max<int64_t>(20, (int64_t)(0.75 * mc.est_us)));
             {
                 std::lock_guard<std::mutex> lk(S->mu);
                 if (rc != TABNET_OK && S->error == TABNET_OK) S->error = rc;
@@ -425,10 +448,17 @@ void engine_loop(tabnet_server* S) {
             }
             did = true;
         }
+        {
+            const double pass_ms = std::chrono::duration<double, std::milli>(Clock::now() - t_pass).count();
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->engine_max_pass_ms = std::max(S->engine_max_pass_ms, pass_ms);
+        }
         if (!did) {
             std::unique_lock<std::mutex> lk(S->mu);
             S->engine_idle.store(true, std::memory_order_relaxed);
+            const auto t_sleep = Clock::now();
             S->cv.wait_for(lk, std::chrono::microseconds(50));
+            S->engine_sleep_s += std::chrono::duration<double>(Clock::now() - t_sleep).count();
             S->engine_idle.store(false, std::memory_order_relaxed);
         }
     }
@@ -448,8 +478,9 @@ int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet
     S->cfg.max_batch_rows = cfg && cfg->max_batch_rows > 0 ? cfg->max_batch_rows : 65536;
     S->cfg.max_inflight_batches = cfg && cfg->max_inflight_batches > 0 ? cfg->max_inflight_batches : 32;
     S->cfg.streams_per_model = cfg && cfg->streams_per_model > 0 ? std::min(cfg->streams_per_model, 64) : 8;
-    S->cfg.batch_min_rows = cfg && cfg->batch_min_rows != 0 ? cfg->batch_min_rows : 512;
+    S->cfg.batch_min_rows = cfg && cfg->batch_min_rows != 0 ? cfg->batch_min_rows : 2048;
     S->cfg.batch_wait_us = cfg && cfg->batch_wait_us > 0 ? cfg->batch_wait_us : 200;
+    S->cfg.batch_busy = cfg && cfg->batch_busy > 0 ? cfg->batch_busy : 2;
     S->cfg.mask_slots = cfg ? cfg->mask_slots : 0;
     S->device = models[0]->device;
     int prev = 0;
@@ -529,8 +560,9 @@ int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet
     return TABNET_OK;
 }
 
-int tabnet_server_submit(tabnet_server* S, int model, const float* x_num, const int32_t* x_cat, int64_t rows,
-                         uint64_t* ticket) {
+namespace {
+int submit_at(tabnet_server* S, int model, const float* x_num, const int32_t* x_cat, int64_t rows,
+              Clock::time_point t_arrival, uint64_t* ticket) {
     if (!S || !ticket || model < 0 || model >= (int)S->models.size() || rows <= 0)
         return tabnet::set_last_error(TABNET_ERR_ARG, "bad server, model index, rows or ticket pointer");
     const tabnet_dims& d = S->models[model].d;
@@ -541,6 +573,7 @@ int tabnet_server_submit(tabnet_server* S, int model, const float* x_num, const 
     r->x_num = x_num;
     r->x_cat = x_cat;
     r->rows = rows;
+    r->t_arrival = t_arrival;
     r->t_submit = Clock::now();
     r->ticket = S->next_ticket.fetch_add(1);
     ModelCtx& mc = S->models[model];
@@ -578,6 +611,12 @@ int tabnet_server_submit(tabnet_server* S, int model, const float* x_num, const 
     if (S->engine_idle.load(std::memory_order_relaxed)) S->cv.notify_all();
     *ticket = r->ticket;
     return TABNET_OK;
+}
+}  // namespace
+
+int tabnet_server_submit(tabnet_server* S, int model, const float* x_num, const int32_t* x_cat, int64_t rows,
+                         uint64_t* ticket) {
+    return submit_at(S, model, x_num, x_cat, rows, Clock::now(), ticket);
 }
 
 int tabnet_server_poll(tabnet_server* S, uint64_t* tickets, int max_tickets, int* n_done) {
@@ -714,10 +753,12 @@ int tabnet_server_wait(tabnet_server* S, uint64_t ticket, double timeout_s) {
 
 int tabnet_server_get_stats(tabnet_server* S, tabnet_server_stats* st) {
     if (!S || !st) return tabnet::set_last_error(TABNET_ERR_ARG, "null pointer");
-    std::vector<double> lat;
+    std::vector<double> lat, qms, sms;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         lat = S->lat_ms;
+        qms = S->queue_ms;
+        sms = S->sub_ms;
         st->submitted = S->submitted;
         st->completed = S->n_completed;
         st->rejected = S->rejected;
@@ -737,6 +778,9 @@ int tabnet_server_get_stats(tabnet_server* S, tabnet_server_stats* st) {
         st->engine_staged = S->engine_staged;
         const double secs = std::chrono::duration<double>(Clock::now() - S->t_reset).count();
         st->rows_per_s = secs > 0 ? S->rows_done / secs : 0.0;
+        st->engine_busy = secs > 0 ? std::max(0.0, 1.0 - S->engine_sleep_s / secs) : 0.0;
+        st->engine_max_pass_ms = S->engine_max_pass_ms;
+        st->replay_max_late_ms = S->replay_max_late_ns.load() * 1e-6;
     }
     std::sort(lat.begin(), lat.end());
     auto pct = [&](double q) { return lat.empty() ? 0.0 : lat[std::min(lat.size() - 1, (size_t)(q * (lat.size() - 1) + 0.5))]; };
@@ -747,6 +791,14 @@ int tabnet_server_get_stats(tabnet_server* S, tabnet_server_stats* st) {
     double sum = 0;
     for (double v : lat) sum += v;
     st->mean_ms = lat.empty() ? 0.0 : sum / lat.size();
+    std::sort(qms.begin(), qms.end());
+    auto qpct = [&](double q) { return qms.empty() ? 0.0 : qms[std::min(qms.size() - 1, (size_t)(q * (qms.size() - 1) + 0.5))]; };
+    st->p50_queue_ms = qpct(0.50);
+    st->p99_queue_ms = qpct(0.99);
+    std::sort(sms.begin(), sms.end());
+    auto spct = [&](double q) { return sms.empty() ? 0.0 : sms[std::min(sms.size() - 1, (size_t)(q * (sms.size() - 1) + 0.5))]; };
+    st->p50_submit_ms = spct(0.50);
+    st->p99_submit_ms = spct(0.99);
     return S->error;
 }
 
@@ -754,41 +806,81 @@ int tabnet_server_reset_stats(tabnet_server* S) {
     if (!S) return tabnet::set_last_error(TABNET_ERR_ARG, "null server");
     std::lock_guard<std::mutex> lk(S->mu);
     S->lat_ms.clear();
+    S->queue_ms.clear();
+    S->sub_ms.clear();
+    S->engine_sleep_s = 0;
+    S->engine_max_pass_ms = 0;
+    S->replay_max_late_ns = 0;
     S->submitted = S->n_completed = S->rejected = S->rows_done = S->batches = S->batch_rows = S->engine_staged = 0;
     S->t_reset = Clock::now();
     return TABNET_OK;
 }
 
-int tabnet_server_replay(tabnet_server* S, const tabnet_server_request* reqs, int n, int release) {
+int tabnet_server_replay(tabnet_server* S, const tabnet_server_request* reqs, int n, int release, int threads) {
     if (!S || (n > 0 && !reqs) || n < 0) return tabnet::set_last_error(TABNET_ERR_ARG, "bad arguments");
+    if (threads <= 0) threads = 1;
+    threads = std::min(threads, 64);
     const auto t0 = Clock::now();
-    std::vector<uint64_t> done(1024);
-    // Release finished requests while waiting for the next arrival, at most
-    // every 20 us: polling on every spin would contend for the engine's lock.
-    auto last_poll = t0;
-    for (int i = 0; i < n; ++i) {
-        const auto due = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(reqs[i].arrival_s));
-        for (auto now = Clock::now(); now < due; now = Clock::now()) {
-            if (release && now - last_poll >= std::chrono::microseconds(20)) {
-                last_poll = now;
-                int k = 0;
-                tabnet_server_poll(S, done.data(), (int)done.size(), &k);
-                release_group(S, done.data(), k);
+    // Release finished requests every 20 us (one thread at a time) -- while
+    // waiting for the next arrival and also between submissions when behind
+    // schedule: a client that only releases when it has time to spare stops
+    // freeing output memory exactly when a burst has put it behind, and the
+    // batches that would clear the burst then wait for that memory.
+    // (Polling on every spin would contend for the engine's lock.)
+    std::atomic<int64_t> last_poll{0};  // ns since t0
+    std::atomic<int> first_error{TABNET_OK};
+    auto poll_release = [&](std::vector<uint64_t>& done, Clock::time_point now) {
+        const int64_t t = std::chrono::duration_cast<std::chrono::nanoseconds>(now - t0).count();
+        int64_t last = last_poll.load(std::memory_order_relaxed);
+        if (t - last < 20000 || !last_poll.compare_exchange_strong(last, t)) return;
+        int k = 0;
+        tabnet_server_poll(S, done.data(), (int)done.size(), &k);
+        release_group(S, done.data(), k);
+    };
+    // Submitting thread j takes requests j, j + T, j + 2T, ... in order; each
+    // is submitted at its arrival offset and its latency counts from there.
+    auto drive = [&](int j) {
+        std::vector<uint64_t> done(1024);
+        for (int i = j; i < n && first_error.load(std::memory_order_relaxed) == TABNET_OK; i += threads) {
+            const auto due =
+                t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(reqs[i].arrival_s));
+            for (auto now = Clock::now();; now = Clock::now()) {
+                if (release) poll_release(done, now);
+                if (now >= due) break;
+            }
+            const int64_t late = std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - due).count();
+            for (int64_t m = S->replay_max_late_ns.load(std::memory_order_relaxed);
+                 late > m && !S->replay_max_late_ns.compare_exchange_weak(m, late);) {
+            }
+            uint64_t t;
+            const int rc = submit_at(S, reqs[i].model, reqs[i].x_num, reqs[i].x_cat, reqs[i].rows, due, &t);
+            if (rc != TABNET_OK) {
+                int ok = TABNET_OK;
+                first_error.compare_exchange_strong(ok, rc);
             }
         }
-        uint64_t t;
-        int rc = tabnet_server_submit(S, reqs[i].model, reqs[i].x_num, reqs[i].x_cat, reqs[i].rows, &t);
-        if (rc != TABNET_OK) return rc;
+    };
+    if (threads == 1) {
+        drive(0);
+    } else {
+        std::vector<std::thread> pool;
+        for (int j = 0; j < threads; ++j) pool.emplace_back(drive, j);
+        for (auto& th : pool) th.join();
     }
+    if (first_error.load() != TABNET_OK) return first_error.load();
     if (release) {  // drain
+        std::vector<uint64_t> done(1024);
         while (true) {
             int k = 0;
             const int rc = tabnet_server_poll(S, done.data(), (int)done.size(), &k);
             release_group(S, done.data(), k);
             if (rc != TABNET_OK) return rc;
-            tabnet_server_stats st;
-            tabnet_server_get_stats(S, &st);
-            if (st.completed + st.rejected >= st.submitted && k == 0) break;
+            bool all_done;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                all_done = S->n_completed + S->rejected >= S->submitted;
+            }
+            if (all_done && k == 0) break;
             std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
     }

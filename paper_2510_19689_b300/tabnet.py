@@ -72,7 +72,8 @@ def segment_array(segs):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_size_t), ("max_batch_rows", ctypes.c_int),
                 ("max_inflight_batches", ctypes.c_int), ("streams_per_model", ctypes.c_int),
-                ("batch_min_rows", ctypes.c_int), ("batch_wait_us", ctypes.c_int), ("mask_slots", ctypes.c_int)]
+                ("batch_min_rows", ctypes.c_int), ("batch_wait_us", ctypes.c_int), ("batch_busy", ctypes.c_int),
+                ("mask_slots", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -82,7 +83,10 @@ class ServerStats(ctypes.Structure):
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("rows_per_s", ctypes.c_double), ("queue_depth", ctypes.c_int64),
                 ("inflight_batches", ctypes.c_int64), ("device_bytes_in_use", ctypes.c_size_t),
-                ("engine_staged", ctypes.c_uint64)]
+                ("engine_staged", ctypes.c_uint64), ("p50_queue_ms", ctypes.c_double),
+                ("p99_queue_ms", ctypes.c_double), ("engine_busy", ctypes.c_double),
+                ("engine_max_pass_ms", ctypes.c_double), ("replay_max_late_ms", ctypes.c_double),
+                ("p50_submit_ms", ctypes.c_double), ("p99_submit_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -148,7 +152,7 @@ def lib() -> ctypes.CDLL:
     L.tabnet_server_release.argtypes = [vp, ctypes.c_uint64]
     L.tabnet_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
     L.tabnet_server_reset_stats.argtypes = [vp]
-    L.tabnet_server_replay.argtypes = [vp, ctypes.POINTER(ServerRequest), i32, i32]
+    L.tabnet_server_replay.argtypes = [vp, ctypes.POINTER(ServerRequest), i32, i32, i32]
     L.tabnet_server_destroy.argtypes = [vp]
     L.tabnet_server_destroy.restype = None
     L.tabnet_destroy.argtypes = [vp]
@@ -309,11 +313,11 @@ class Server:
     (tabnet_server_*).  Inputs are numpy arrays kept alive until release."""
 
     def __init__(self, models, device_bytes=1 << 30, max_batch_rows=65536, max_inflight_batches=32,
-                 streams_per_model=8, batch_min_rows=512, batch_wait_us=200, mask_slots=0):
+                 streams_per_model=8, batch_min_rows=0, batch_wait_us=0, mask_slots=0, batch_busy=0):
         self.models = list(models)
         arr = (ctypes.c_void_p * len(self.models))(*[m.handle for m in self.models])
         cfg = ServerConfig(device_bytes, max_batch_rows, max_inflight_batches, streams_per_model, batch_min_rows,
-                           batch_wait_us, mask_slots)
+                           batch_wait_us, batch_busy, mask_slots)
         h = ctypes.c_void_p()
         _check(lib().tabnet_server_create(arr, len(self.models), ctypes.byref(cfg), ctypes.byref(h)),
                "tabnet_server_create")
@@ -399,13 +403,15 @@ class Server:
             arr[i] = ServerRequest(model, _ptr(xn) if d.n_num else None, _ptr(xc) if d.n_cat else None, rows, t)
         return arr, keep
 
-    def replay_prepared(self, prepared, release: bool = True) -> None:
+    def replay_prepared(self, prepared, release: bool = True, threads: int = 1) -> None:
         arr, _ = prepared
-        _check(lib().tabnet_server_replay(self._h, arr, len(arr), 1 if release else 0), "tabnet_server_replay")
+        _check(lib().tabnet_server_replay(self._h, arr, len(arr), 1 if release else 0, threads),
+               "tabnet_server_replay")
 
-    def replay(self, requests, release: bool = True) -> None:
-        """requests: list of (model, x_num, x_cat, arrival_s) with numpy inputs."""
-        self.replay_prepared(self.prepare_replay(requests), release)
+    def replay(self, requests, release: bool = True, threads: int = 1) -> None:
+        """requests: list of (model, x_num, x_cat, arrival_s) with numpy inputs;
+        `threads` submitting threads (clients)."""
+        self.replay_prepared(self.prepare_replay(requests), release, threads)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -117,7 +117,8 @@ def test_admission_waits_for_memory(models):
     srv.close()
 
 
-def test_poisson_replay(models):
+@pytest.mark.parametrize("threads", [1, 4])
+def test_poisson_replay(models, threads):
     tabnet, params, ms = models
     srv = tabnet.Server(ms, device_bytes=512 << 20)
     rng = np.random.default_rng(9)
@@ -131,11 +132,14 @@ def test_poisson_replay(models):
         xn, xc = pools[i]
         reqs.append((i, xn[:sizes[k]], xc[:sizes[k]], float(t[k])))
     srv.reset_stats()
-    srv.replay(reqs)
+    srv.replay(reqs, threads=threads)
     st = srv.stats()
     assert st["completed"] == n_req and st["rejected"] == 0
     assert st["rows_completed"] == int(sizes.sum())
     assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
+    # every request's wait for its launch is part of its latency
+    assert 0 <= st["p50_queue_ms"] <= st["p50_ms"] and st["p99_queue_ms"] <= st["p99_ms"]
+    assert 0.0 <= st["engine_busy"] <= 1.0
     srv.close()
 
 
