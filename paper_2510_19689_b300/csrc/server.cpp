@@ -37,6 +37,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <pthread.h>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -142,11 +143,38 @@ constexpr size_t kRegionSlack = 6 * 256;  // alignment of the six arrays of an o
 
 }  // namespace
 
+namespace {
+// The server lock: a pthread mutex of the adaptive kind, which spins
+// briefly before it sleeps.  Its critical sections are short and taken
+// hundreds of thousands of times a second by the clients and the engine; a
+// plain mutex puts every contender to sleep at once, and the wake-ups queue
+// submissions behind each other.
+class ServerMutex {
+public:
+    ServerMutex() {
+        pthread_mutexattr_t a;
+        pthread_mutexattr_init(&a);
+        pthread_mutexattr_settype(&a, PTHREAD_MUTEX_ADAPTIVE_NP);
+        pthread_mutex_init(&m_, &a);
+        pthread_mutexattr_destroy(&a);
+    }
+    ~ServerMutex() { pthread_mutex_destroy(&m_); }
+    ServerMutex(const ServerMutex&) = delete;
+    ServerMutex& operator=(const ServerMutex&) = delete;
+    void lock() { pthread_mutex_lock(&m_); }
+    bool try_lock() { return pthread_mutex_trylock(&m_) == 0; }
+    void unlock() { pthread_mutex_unlock(&m_); }
+
+private:
+    pthread_mutex_t m_;
+};
+}  // namespace
+
 struct tabnet_server {
     std::vector<ModelCtx> models;
     tabnet_server_config cfg{};
-    std::mutex mu;                       // guards pending queues, requests, stats
-    std::condition_variable cv;
+    ServerMutex mu;                      // guards pending queues, requests, stats
+    std::condition_variable_any cv;
     std::unordered_map<uint64_t, Request*> reqs;
     std::atomic<uint64_t> next_ticket{1};
     std::deque<uint64_t> completed;      // tickets completed, not yet returned by poll
@@ -291,7 +319,7 @@ void engine_loop(tabnet_server* S) {
                     }
                 }
                 const auto now = Clock::now();
-                std::lock_guard<std::mutex> lk(S->mu);
+                std::lock_guard<ServerMutex> lk(S->mu);
                 b->complete = true;
                 --mc.running;
                 for (uint64_t t : b->tickets) {
@@ -308,7 +336,7 @@ void engine_loop(tabnet_server* S) {
                 if (q != cudaSuccess && S->error == TABNET_OK) S->error = TABNET_ERR_CUDA;
                 did = true;
             }
-            std::lock_guard<std::mutex> lk(S->mu);
+            std::lock_guard<ServerMutex> lk(S->mu);
             // input rows of finished batches go back at once, in ring order
             while (!mc.in_order.empty() && mc.in_order.front()->complete) {
                 Batch* b = mc.in_order.front();
@@ -337,7 +365,7 @@ void engine_loop(tabnet_server* S) {
             int64_t rows = 0;
             size_t off = 0, bytes = 0;
             {
-                std::lock_guard<std::mutex> lk(S->mu);
+                std::lock_guard<ServerMutex> lk(S->mu);
                 // only batches still on the GPU count; finished results hold ring memory instead
                 if (mc.pending.empty() || mc.running >= S->cfg.max_inflight_batches) continue;
                 // Under load (batch_busy of the model's batches running) a small
@@ -438,7 +466,7 @@ void engine_loop(tabnet_server* S) {
             b->t_launch = Clock::now();
             b->next_query = b->t_launch + std::chrono::microseconds(std::max<int64_t>(20, (int64_t)(0.75 * mc.est_us)));
             {
-                std::lock_guard<std::mutex> lk(S->mu);
+                std::lock_guard<ServerMutex> lk(S->mu);
                 if (rc != TABNET_OK && S->error == TABNET_OK) S->error = rc;
                 mc.inflight.push_back(b);
                 mc.in_order.push_back(b);
@@ -450,11 +478,11 @@ void engine_loop(tabnet_server* S) {
         }
         {
             const double pass_ms = std::chrono::duration<double, std::milli>(Clock::now() - t_pass).count();
-            std::lock_guard<std::mutex> lk(S->mu);
+            std::lock_guard<ServerMutex> lk(S->mu);
             S->engine_max_pass_ms = std::max(S->engine_max_pass_ms, pass_ms);
         }
         if (!did) {
-            std::unique_lock<std::mutex> lk(S->mu);
+            std::unique_lock<ServerMutex> lk(S->mu);
             S->engine_idle.store(true, std::memory_order_relaxed);
             const auto t_sleep = Clock::now();
             S->cv.wait_for(lk, std::chrono::microseconds(50));
@@ -582,7 +610,7 @@ int submit_at(tabnet_server* S, int model, const float* x_num, const int32_t* x_
     Request* to_stage[8];
     int n_stage = 0;
     {
-        std::lock_guard<std::mutex> lk(S->mu);
+        std::lock_guard<ServerMutex> lk(S->mu);
         S->reqs.emplace(r->ticket, r);
         mc.unstaged.push_back(r);
         // The inputs go to the input ring in submission order.  A request
@@ -621,7 +649,7 @@ int tabnet_server_submit(tabnet_server* S, int model, const float* x_num, const 
 
 int tabnet_server_poll(tabnet_server* S, uint64_t* tickets, int max_tickets, int* n_done) {
     if (!S || !n_done || (max_tickets > 0 && !tickets)) return tabnet::set_last_error(TABNET_ERR_ARG, "null pointer");
-    std::lock_guard<std::mutex> lk(S->mu);
+    std::lock_guard<ServerMutex> lk(S->mu);
     int n = 0;
     while (n < max_tickets && !S->completed.empty()) {
         tickets[n++] = S->completed.front();
@@ -639,7 +667,7 @@ int tabnet_server_result(tabnet_server* S, uint64_t ticket, const float** logits
     Batch* b = nullptr;
     int slots = 0;
     {
-        std::lock_guard<std::mutex> lk(S->mu);
+        std::lock_guard<ServerMutex> lk(S->mu);
         auto it = S->reqs.find(ticket);
         if (it == S->reqs.end() || !it->second->batch || !it->second->batch->complete)
             return tabnet::set_last_error(TABNET_ERR_ARG, "ticket unknown, released or not complete");
@@ -678,7 +706,7 @@ int tabnet_server_result(tabnet_server* S, uint64_t ticket, const float** logits
 int tabnet_server_result_compact(tabnet_server* S, uint64_t ticket, const uint8_t** counts, const uint16_t** cols,
                                  const float** vals, int* slots, int64_t* rows) {
     if (!S || !counts || !cols || !vals || !slots) return tabnet::set_last_error(TABNET_ERR_ARG, "null pointer");
-    std::lock_guard<std::mutex> lk(S->mu);
+    std::lock_guard<ServerMutex> lk(S->mu);
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end() || !it->second->batch || !it->second->batch->complete)
         return tabnet::set_last_error(TABNET_ERR_ARG, "ticket unknown, released or not complete");
@@ -719,7 +747,7 @@ int release_locked(tabnet_server* S, uint64_t ticket) {
 void release_group(tabnet_server* S, const uint64_t* tickets, int k) {
     if (k <= 0) return;
     {
-        std::lock_guard<std::mutex> lk(S->mu);
+        std::lock_guard<ServerMutex> lk(S->mu);
         for (int j = 0; j < k; ++j) release_locked(S, tickets[j]);
     }
     if (S->engine_idle.load(std::memory_order_relaxed)) S->cv.notify_all();
@@ -730,7 +758,7 @@ int tabnet_server_release(tabnet_server* S, uint64_t ticket) {
     if (!S) return tabnet::set_last_error(TABNET_ERR_ARG, "null server");
     int rc;
     {
-        std::lock_guard<std::mutex> lk(S->mu);
+        std::lock_guard<ServerMutex> lk(S->mu);
         rc = release_locked(S, ticket);
     }
     if (rc == TABNET_OK && S->engine_idle.load(std::memory_order_relaxed)) S->cv.notify_all();
@@ -739,7 +767,7 @@ int tabnet_server_release(tabnet_server* S, uint64_t ticket) {
 
 int tabnet_server_wait(tabnet_server* S, uint64_t ticket, double timeout_s) {
     if (!S) return tabnet::set_last_error(TABNET_ERR_ARG, "null server");
-    std::unique_lock<std::mutex> lk(S->mu);
+    std::unique_lock<ServerMutex> lk(S->mu);
     const auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s);
     while (true) {
         auto it = S->reqs.find(ticket);
@@ -755,7 +783,7 @@ int tabnet_server_get_stats(tabnet_server* S, tabnet_server_stats* st) {
     if (!S || !st) return tabnet::set_last_error(TABNET_ERR_ARG, "null pointer");
     std::vector<double> lat, qms, sms;
     {
-        std::lock_guard<std::mutex> lk(S->mu);
+        std::lock_guard<ServerMutex> lk(S->mu);
         lat = S->lat_ms;
         qms = S->queue_ms;
         sms = S->sub_ms;
@@ -804,7 +832,7 @@ int tabnet_server_get_stats(tabnet_server* S, tabnet_server_stats* st) {
 
 int tabnet_server_reset_stats(tabnet_server* S) {
     if (!S) return tabnet::set_last_error(TABNET_ERR_ARG, "null server");
-    std::lock_guard<std::mutex> lk(S->mu);
+    std::lock_guard<ServerMutex> lk(S->mu);
     S->lat_ms.clear();
     S->queue_ms.clear();
     S->sub_ms.clear();
@@ -877,7 +905,7 @@ int tabnet_server_replay(tabnet_server* S, const tabnet_server_request* reqs, in
             if (rc != TABNET_OK) return rc;
             bool all_done;
             {
-                std::lock_guard<std::mutex> lk(S->mu);
+                std::lock_guard<ServerMutex> lk(S->mu);
                 all_done = S->n_completed + S->rejected >= S->submitted;
             }
             if (all_done && k == 0) break;
