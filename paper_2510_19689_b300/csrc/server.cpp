@@ -502,6 +502,9 @@ int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet
     *out = nullptr;
     tabnet_server* S = new (std::nothrow) tabnet_server();
     if (!S) return tabnet::set_last_error(TABNET_ERR_OOM, "host allocation failed");
+    // buckets for the requests a loaded server holds, so that the ticket map
+    // is not rehashed (all of it, under the server lock) as a backlog grows
+    S->reqs.reserve(1 << 16);
     S->cfg.device_bytes = cfg && cfg->device_bytes ? cfg->device_bytes : ((size_t)1 << 30);
     S->cfg.max_batch_rows = cfg && cfg->max_batch_rows > 0 ? cfg->max_batch_rows : 65536;
     S->cfg.max_inflight_batches = cfg && cfg->max_inflight_batches > 0 ? cfg->max_inflight_batches : 32;
@@ -634,9 +637,10 @@ int submit_at(tabnet_server* S, int model, const float* x_num, const int32_t* x_
     // the copies run on the submitting thread, outside the lock; the engine
     // takes a request into a batch once it is marked ready
     for (int i = 0; i < n_stage; ++i) stage_inputs(mc, to_stage[i]);
-    // a wake-up only when the engine sleeps (a missed one costs at most its
-    // 50 us nap): a notify is a system call, and submit runs per request
-    if (S->engine_idle.load(std::memory_order_relaxed)) S->cv.notify_all();
+    // a wake-up only when the engine sleeps, and by one caller per nap (a
+    // missed one costs at most its 50 us nap): a notify takes the condition
+    // variable's own lock and makes a system call, and submit runs per request
+    if (S->engine_idle.exchange(false, std::memory_order_relaxed)) S->cv.notify_all();
     *ticket = r->ticket;
     return TABNET_OK;
 }
@@ -732,25 +736,39 @@ int tabnet_server_result_compact(tabnet_server* S, uint64_t ticket, const uint8_
 
 namespace {
 // Release one ticket (the server lock held).
-int release_locked(tabnet_server* S, uint64_t ticket) {
+int release_locked(tabnet_server* S, uint64_t ticket, Request** freed = nullptr) {
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end() || !it->second->batch || !it->second->batch->complete)
         return tabnet::set_last_error(TABNET_ERR_ARG, "ticket unknown, released or not complete");
     it->second->batch->released++;
-    delete it->second;
+    if (freed) *freed = it->second;  // the caller deletes it outside the lock
+    else delete it->second;
     S->reqs.erase(it);
     return TABNET_OK;
 }
 
-// Release k tickets under one acquisition of the lock (the load driver's
-// path: one lock per ticket would contend with the engine at high rates).
+// Release k tickets, at most 32 under one acquisition of the lock (the load
+// driver's path: one lock per ticket would contend with the engine at high
+// rates, and a whole poll's worth -- up to a thousand after a burst -- would
+// hold the clients' submissions for most of a millisecond); the requests'
+// memory is freed outside the lock.
 void release_group(tabnet_server* S, const uint64_t* tickets, int k) {
     if (k <= 0) return;
-    {
-        std::lock_guard<ServerMutex> lk(S->mu);
-        for (int j = 0; j < k; ++j) release_locked(S, tickets[j]);
+    constexpr int kGroup = 32;
+    Request* freed[kGroup];
+    for (int j0 = 0; j0 < k; j0 += kGroup) {
+        const int n = std::min(kGroup, k - j0);
+        int nf = 0;
+        {
+            std::lock_guard<ServerMutex> lk(S->mu);
+            for (int j = 0; j < n; ++j) {
+                Request* r = nullptr;
+                if (release_locked(S, tickets[j0 + j], &r) == TABNET_OK) freed[nf++] = r;
+            }
+        }
+        for (int j = 0; j < nf; ++j) delete freed[j];
     }
-    if (S->engine_idle.load(std::memory_order_relaxed)) S->cv.notify_all();
+    if (S->engine_idle.exchange(false, std::memory_order_relaxed)) S->cv.notify_all();
 }
 }  // namespace
 
@@ -761,7 +779,7 @@ int tabnet_server_release(tabnet_server* S, uint64_t ticket) {
         std::lock_guard<ServerMutex> lk(S->mu);
         rc = release_locked(S, ticket);
     }
-    if (rc == TABNET_OK && S->engine_idle.load(std::memory_order_relaxed)) S->cv.notify_all();
+    if (rc == TABNET_OK && S->engine_idle.exchange(false, std::memory_order_relaxed)) S->cv.notify_all();
     return rc;
 }
 
