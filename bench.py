@@ -114,13 +114,14 @@ def profiled_traffic(workload, precision):
 
 class ClockSampler:
     """SM clock, power and throttle reasons sampled while running: through
-    NVML every `period_s` (1 ms by default, so that even a few-millisecond
-    timed region is sampled), else through nvidia-smi every 200 ms."""
+    NVML every `period_s` (0.25 ms by default, so that even a few-millisecond
+    timed region is sampled several times), else through nvidia-smi every
+    200 ms."""
 
     REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
                ("sw_power_cap", 0x4))
 
-    def __init__(self, device, period_s=0.001):
+    def __init__(self, device, period_s=0.00025):
         self.device = device
         self.period_s = period_s
         self.samples = []  # (sm_mhz, max_sm_mhz, power_w, reason bits)
@@ -165,9 +166,15 @@ class ClockSampler:
             self.stop = threading.Event()
 
             def run():
+                # the clock and the reasons every period; the power reading
+                # (a slower query) at most every 20 ms, so that a timed
+                # region of a few milliseconds still gets several samples
+                t_pw = -1.0
                 while not self.stop.is_set():
+                    now = time.perf_counter()
+                    if now - t_pw >= 0.02 and lib.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw)) == 0:
+                        t_pw = now
                     if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(sm)) == 0
-                            and lib.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw)) == 0
                             and reasons(h, ctypes.byref(rs)) == 0):
                         self.samples.append((float(sm.value), float(mx.value), pw.value / 1000.0, int(rs.value)))
                     self.stop.wait(self.period_s)
@@ -341,7 +348,7 @@ def fp8_gemm_peak(dev, n=8192, reps=10):
 
 def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), seconds=1.0,
                   streams_per_model=16, max_inflight_batches=32, batch_min_rows=2048, batch_wait_us=200,
-                  clients=4, batch_busy=2):
+                  clients=8, batch_busy=2):
     """Poisson arrivals at each rate for `seconds`, request sizes
     floor(exp(U(0, ln 513))) in [1, 512] rows, the three model shapes
     resident (split-bf16), model chosen uniformly, submitted by `clients`
