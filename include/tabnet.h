@@ -299,7 +299,9 @@ typedef struct {
     double mean_batch_rows;
     double p50_ms, p95_ms, p99_ms, mean_ms, max_ms;  /* latency of completed requests: completion seen
                                                         on the host - arrival (submission, or a replayed
-                                                        request's scheduled arrival) */
+                                                        request's scheduled arrival); every percentile
+                                                        of these stats is over the most recent 1,048,576
+                                                        requests completed since the reset */
     double rows_per_s;                               /* completed rows / time since reset */
     int64_t queue_depth, inflight_batches;
     size_t device_bytes_in_use;

@@ -144,6 +144,21 @@ constexpr size_t kRegionSlack = 6 * 256;  // alignment of the six arrays of an o
 }  // namespace
 
 namespace {
+// Latency samples for the percentiles: the most recent kCap values (a ring
+// once full), so that a server that runs for hours without a reset keeps a
+// bounded record.
+struct Samples {
+    static constexpr size_t kCap = (size_t)1 << 20;
+    std::vector<double> v;
+    size_t n = 0;  // values pushed since the last clear
+    void push(double x) {
+        if (v.size() < kCap) v.push_back(x);
+        else v[n % kCap] = x;
+        ++n;
+    }
+    void clear() { v.clear(); n = 0; }
+};
+
 // The server lock: a pthread mutex of the adaptive kind, which spins
 // briefly before it sleeps.  Its critical sections are short and taken
 // hundreds of thousands of times a second by the clients and the engine; a
@@ -178,9 +193,9 @@ struct tabnet_server {
     std::unordered_map<uint64_t, Request*> reqs;
     std::atomic<uint64_t> next_ticket{1};
     std::deque<uint64_t> completed;      // tickets completed, not yet returned by poll
-    std::vector<double> lat_ms;          // completed requests' latencies since the last reset
-    std::vector<double> queue_ms;        // their arrival -> batch launch times
-    std::vector<double> sub_ms;          // their submission call -> completion times
+    Samples lat_ms;                      // completed requests' latencies since the last reset
+    Samples queue_ms;                    // their arrival -> batch launch times
+    Samples sub_ms;                      // their submission call -> completion times
     double engine_sleep_s = 0;           // engine time asleep on cv since the last reset
     double engine_max_pass_ms = 0;       // longest engine pass (completions + launches) since the reset
     std::atomic<int64_t> replay_max_late_ns{0};  // latest replayed submission behind its arrival
@@ -325,9 +340,9 @@ void engine_loop(tabnet_server* S) {
                 for (uint64_t t : b->tickets) {
                     auto it = S->reqs.find(t);
                     if (it == S->reqs.end()) continue;
-                    S->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - it->second->t_arrival).count());
-                    S->sub_ms.push_back(std::chrono::duration<double, std::milli>(now - it->second->t_submit).count());
-                    S->queue_ms.push_back(
+                    S->lat_ms.push(std::chrono::duration<double, std::milli>(now - it->second->t_arrival).count());
+                    S->sub_ms.push(std::chrono::duration<double, std::milli>(now - it->second->t_submit).count());
+                    S->queue_ms.push(
                         std::chrono::duration<double, std::milli>(b->t_launch - it->second->t_arrival).count());
                     S->completed.push_back(t);
                     S->rows_done += it->second->rows;
@@ -802,9 +817,9 @@ int tabnet_server_get_stats(tabnet_server* S, tabnet_server_stats* st) {
     std::vector<double> lat, qms, sms;
     {
         std::lock_guard<ServerMutex> lk(S->mu);
-        lat = S->lat_ms;
-        qms = S->queue_ms;
-        sms = S->sub_ms;
+        lat = S->lat_ms.v;
+        qms = S->queue_ms.v;
+        sms = S->sub_ms.v;
         st->submitted = S->submitted;
         st->completed = S->n_completed;
         st->rejected = S->rejected;
