@@ -346,10 +346,12 @@ def fp8_gemm_peak(dev, n=8192, reps=10):
         return {"value": None, "unavailable": str(exc)[:200]}
 
 
-def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), seconds=1.0,
+def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), seconds=None,
                   streams_per_model=16, max_inflight_batches=32, batch_min_rows=2048, batch_wait_us=200,
                   clients=8, batch_busy=2):
-    """Poisson arrivals at each rate for `seconds`, request sizes
+    """Poisson arrivals at each rate for `seconds` (default: long enough
+    for 100,000 requests, at least 1 s and at most 10 s; the first 10 % of
+    the requests are warm-up, left out of the latency statistics), request sizes
     floor(exp(U(0, ln 513))) in [1, 512] rows, the three model shapes
     resident (split-bf16), model chosen uniformly, submitted by `clients`
     threads; the server's latency (completion seen on the host - scheduled
@@ -366,7 +368,9 @@ def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), s
     out = []
     for rate in rates:
         rng = np.random.default_rng(rate)
-        n = int(rate * seconds)
+        secs = seconds if seconds is not None else min(10.0, max(1.0, 1e5 / rate))
+        n = int(rate * secs)
+        warm = n // 10
         t = np.cumsum(rng.exponential(1.0 / rate, n))
         sizes = np.clip(np.floor(np.exp(rng.uniform(0, math.log(513), n))), 1, 512).astype(int)
         which = rng.integers(0, 3, n)
@@ -375,10 +379,11 @@ def bench_serving(dev_index, rates=(1000, 5000, 20000, 50000, 100000, 200000), s
         prepared = srv.prepare_replay(reqs)  # marshalling stays outside the timed region
         srv.reset_stats()
         t0 = time.perf_counter()
-        srv.replay_prepared(prepared, threads=clients)
+        srv.replay_prepared(prepared, threads=clients, warmup=warm)
         wall = time.perf_counter() - t0
         st = srv.stats()
-        out.append({"offered_req_per_s": rate, "requests": n, "completed": st["completed"],
+        out.append({"offered_req_per_s": rate, "seconds": secs, "requests": n, "warmup_requests": warm,
+                    "completed": st["completed"],
                     "achieved_req_per_s": st["completed"] / wall, "rows_per_s": st["rows_completed"] / wall,
                     "p50_ms": st["p50_ms"], "p95_ms": st["p95_ms"], "p99_ms": st["p99_ms"],
                     "mean_batch_rows": st["mean_batch_rows"], "batches": st["batches"],

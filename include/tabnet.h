@@ -382,12 +382,14 @@ int tabnet_server_reset_stats(tabnet_server* server);
  * host clock) from `threads` submitting threads (<= 0: 1, at most 64;
  * thread j takes requests j, j + threads, ... in order), standing for that
  * many clients; a replayed request's latency counts from its scheduled
- * arrival, so a submission that comes late counts too.  With `release` != 0
- * completed requests are released as they finish (polled every 20 us,
- * between submissions too when a thread is behind schedule) and the call
- * returns when all are done.  Errors: as tabnet_server_submit. */
+ * arrival, so a submission that comes late counts too.  The first `warmup`
+ * requests are served but left out of the latency statistics (the counts
+ * and row totals include them).  With `release` != 0 completed requests are
+ * released as they finish (polled every 20 us, between submissions too when
+ * a thread is behind schedule) and the call returns when all are done.
+ * Errors: as tabnet_server_submit. */
 int tabnet_server_replay(tabnet_server* server, const tabnet_server_request* reqs, int n, int release,
-                         int threads);
+                         int threads, int warmup);
 
 /* Stop the engine, wait for the GPU, free everything. */
 void tabnet_server_destroy(tabnet_server* server);

@@ -69,6 +69,7 @@ struct Request {
     // arrival (a late submission then counts in its latency)
     Clock::time_point t_arrival;
     Clock::time_point t_submit;  // when the submission call ran
+    bool measured = true;        // in the latency statistics (a replay's warm-up requests are not)
     // rows of the model's input ring holding the inputs (-1: not staged
     // yet), and whether they are copied there
     int64_t in_row0 = -1;
@@ -340,10 +341,12 @@ void engine_loop(tabnet_server* S) {
                 for (uint64_t t : b->tickets) {
                     auto it = S->reqs.find(t);
                     if (it == S->reqs.end()) continue;
-                    S->lat_ms.push(std::chrono::duration<double, std::milli>(now - it->second->t_arrival).count());
-                    S->sub_ms.push(std::chrono::duration<double, std::milli>(now - it->second->t_submit).count());
-                    S->queue_ms.push(
-                        std::chrono::duration<double, std::milli>(b->t_launch - it->second->t_arrival).count());
+                    if (it->second->measured) {
+                        S->lat_ms.push(std::chrono::duration<double, std::milli>(now - it->second->t_arrival).count());
+                        S->sub_ms.push(std::chrono::duration<double, std::milli>(now - it->second->t_submit).count());
+                        S->queue_ms.push(
+                            std::chrono::duration<double, std::milli>(b->t_launch - it->second->t_arrival).count());
+                    }
                     S->completed.push_back(t);
                     S->rows_done += it->second->rows;
                     ++S->n_completed;
@@ -608,7 +611,7 @@ int tabnet_server_create(tabnet_model* const* models, int n_models, const tabnet
 
 namespace {
 int submit_at(tabnet_server* S, int model, const float* x_num, const int32_t* x_cat, int64_t rows,
-              Clock::time_point t_arrival, uint64_t* ticket) {
+              Clock::time_point t_arrival, bool measured, uint64_t* ticket) {
     if (!S || !ticket || model < 0 || model >= (int)S->models.size() || rows <= 0)
         return tabnet::set_last_error(TABNET_ERR_ARG, "bad server, model index, rows or ticket pointer");
     const tabnet_dims& d = S->models[model].d;
@@ -620,6 +623,7 @@ int submit_at(tabnet_server* S, int model, const float* x_num, const int32_t* x_
     r->x_cat = x_cat;
     r->rows = rows;
     r->t_arrival = t_arrival;
+    r->measured = measured;
     r->t_submit = Clock::now();
     r->ticket = S->next_ticket.fetch_add(1);
     ModelCtx& mc = S->models[model];
@@ -663,7 +667,7 @@ int submit_at(tabnet_server* S, int model, const float* x_num, const int32_t* x_
 
 int tabnet_server_submit(tabnet_server* S, int model, const float* x_num, const int32_t* x_cat, int64_t rows,
                          uint64_t* ticket) {
-    return submit_at(S, model, x_num, x_cat, rows, Clock::now(), ticket);
+    return submit_at(S, model, x_num, x_cat, rows, Clock::now(), true, ticket);
 }
 
 int tabnet_server_poll(tabnet_server* S, uint64_t* tickets, int max_tickets, int* n_done) {
@@ -877,7 +881,8 @@ int tabnet_server_reset_stats(tabnet_server* S) {
     return TABNET_OK;
 }
 
-int tabnet_server_replay(tabnet_server* S, const tabnet_server_request* reqs, int n, int release, int threads) {
+int tabnet_server_replay(tabnet_server* S, const tabnet_server_request* reqs, int n, int release, int threads,
+                         int warmup) {
     if (!S || (n > 0 && !reqs) || n < 0) return tabnet::set_last_error(TABNET_ERR_ARG, "bad arguments");
     if (threads <= 0) threads = 1;
     threads = std::min(threads, 64);
@@ -914,7 +919,7 @@ int tabnet_server_replay(tabnet_server* S, const tabnet_server_request* reqs, in
                  late > m && !S->replay_max_late_ns.compare_exchange_weak(m, late);) {
             }
             uint64_t t;
-            const int rc = submit_at(S, reqs[i].model, reqs[i].x_num, reqs[i].x_cat, reqs[i].rows, due, &t);
+            const int rc = submit_at(S, reqs[i].model, reqs[i].x_num, reqs[i].x_cat, reqs[i].rows, due, i >= warmup, &t);
             if (rc != TABNET_OK) {
                 int ok = TABNET_OK;
                 first_error.compare_exchange_strong(ok, rc);

@@ -152,7 +152,7 @@ def lib() -> ctypes.CDLL:
     L.tabnet_server_release.argtypes = [vp, ctypes.c_uint64]
     L.tabnet_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
     L.tabnet_server_reset_stats.argtypes = [vp]
-    L.tabnet_server_replay.argtypes = [vp, ctypes.POINTER(ServerRequest), i32, i32, i32]
+    L.tabnet_server_replay.argtypes = [vp, ctypes.POINTER(ServerRequest), i32, i32, i32, i32]
     L.tabnet_server_destroy.argtypes = [vp]
     L.tabnet_server_destroy.restype = None
     L.tabnet_destroy.argtypes = [vp]
@@ -403,15 +403,16 @@ class Server:
             arr[i] = ServerRequest(model, _ptr(xn) if d.n_num else None, _ptr(xc) if d.n_cat else None, rows, t)
         return arr, keep
 
-    def replay_prepared(self, prepared, release: bool = True, threads: int = 1) -> None:
+    def replay_prepared(self, prepared, release: bool = True, threads: int = 1, warmup: int = 0) -> None:
         arr, _ = prepared
-        _check(lib().tabnet_server_replay(self._h, arr, len(arr), 1 if release else 0, threads),
+        _check(lib().tabnet_server_replay(self._h, arr, len(arr), 1 if release else 0, threads, warmup),
                "tabnet_server_replay")
 
-    def replay(self, requests, release: bool = True, threads: int = 1) -> None:
+    def replay(self, requests, release: bool = True, threads: int = 1, warmup: int = 0) -> None:
         """requests: list of (model, x_num, x_cat, arrival_s) with numpy inputs;
-        `threads` submitting threads (clients)."""
-        self.replay_prepared(self.prepare_replay(requests), release, threads)
+        `threads` submitting threads (clients); the first `warmup` requests
+        are left out of the latency statistics."""
+        self.replay_prepared(self.prepare_replay(requests), release, threads, warmup)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

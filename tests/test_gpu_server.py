@@ -132,7 +132,7 @@ def test_poisson_replay(models, threads):
         xn, xc = pools[i]
         reqs.append((i, xn[:sizes[k]], xc[:sizes[k]], float(t[k])))
     srv.reset_stats()
-    srv.replay(reqs, threads=threads)
+    srv.replay(reqs, threads=threads, warmup=n_req // 10)
     st = srv.stats()
     assert st["completed"] == n_req and st["rejected"] == 0
     assert st["rows_completed"] == int(sizes.sum())
