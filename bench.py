@@ -416,6 +416,15 @@ def bench_latency(dev, calls=200, host_calls=100):
         w.tune()
         out["rows_per_call"] = w.rows
         ms, stats, clocks = w.time(calls, 10)
+        # the same calls back to back with no event between them (the
+        # per-call marks above add a little to every call)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(w.stream)
+        for k in range(calls):
+            w.step(k)
+        e1.record(w.stream)
+        e1.synchronize()
+        ms_plain = e0.elapsed_time(e1)
         lat = []
         for k in range(host_calls):
             t0 = time.perf_counter()
@@ -424,6 +433,7 @@ def bench_latency(dev, calls=200, host_calls=100):
             lat.append(time.perf_counter() - t0)
         lat = np.array(lat) * 1e3
         out["arms"][prec] = {"ms_per_call": ms / calls, "ms_per_call_stats": stats,
+                             "ms_per_call_unmarked": ms_plain / calls,
                              "rows_per_s": w.rows * calls / (ms / 1e3),
                              "host_latency_ms": {"p50": float(np.median(lat)), "p99": float(np.quantile(lat, 0.99))},
                              "tile": w.tile, "clocks": clocks, "parity": w.parity(256)}
