@@ -281,7 +281,9 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
     // the last 16-column chunk of the P / mask / aggregate regions holds 8
     // columns when the mask width leaves at most 8 in it
     const bool tail8 = p.tail8 != 0;
-    const bool m16 = p.m16 != 0;  // step mask kept as fp16 pairs (TMEM budget)
+    // step mask kept as fp16 pairs (TMEM budget); never in a LEAN launch,
+    // whose aggregate fits in TMEM next to fp32 P and mask regions
+    const bool m16 = !LEAN && p.m16 != 0;
     const int dchunks = p.dp / 16;
     // 16 columns of a P / mask / aggregate region (8 in a half chunk, the
     // rest read as 0); the caller waits with tmem_wait_ld
@@ -1095,6 +1097,30 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                 // ---- decision output: acc += ReLU(d) (folded into the logits), eta, aggregate
                 // res becomes ReLU(d) (zero on the attention columns): the next
                 // step's feature transformer starts from its own first layer.
+                // Where TMEM holds the step mask as fp16 pairs and the caller
+                // takes the masks, the aggregate is summed from the fp32 mask
+                // row this row wrote to the output (several CTA barriers ago);
+                // its chunks are loaded one ahead of their use, the first one
+                // here, before the decision's arithmetic.  Not in FP8, whose
+                // masks carry E4M3's error (2^-4) far above fp16's (2^-11),
+                // and whose kernel has no registers to spare for the chunk.
+                const float* mrow32 = (!FP8 && m16 && io.masks && valid) ? io.masks + (size_t)(s - 1) * de : nullptr;
+                const bool mrow32_v4 = mrow32 && (de & 3) == 0 && (reinterpret_cast<uintptr_t>(mrow32) & 15) == 0;
+                float mnext[16];
+                auto load_mrow = [&](int ch) {
+                    if (!mrow32 || ch >= dch) return;
+                    if (mrow32_v4 && ch * 16 + 16 <= de) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float4 v4 = *reinterpret_cast<const float4*>(mrow32 + ch * 16 + 4 * q);
+                            mnext[4 * q] = v4.x; mnext[4 * q + 1] = v4.y; mnext[4 * q + 2] = v4.z; mnext[4 * q + 3] = v4.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) mnext[j] = ch * 16 + j < de ? mrow32[ch * 16 + j] : 0.f;
+                    }
+                };
+                load_mrow(wg);
                 float eta = 0.f;
 #pragma unroll
                 for (int cc = 0; cc < RCH; ++cc) {
@@ -1125,7 +1151,8 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                     lacc[k] += a0 + a1;
                 }
                 eta = xsum(eta, 0.f).x;
-                // aggregate += eta * M (the step's mask as kept in TMEM)
+                // aggregate += eta * M (the step's mask as kept in TMEM, or the
+                // fp32 mask row loaded above)
 #pragma unroll 1
                 for (int ch = wg; ch < dch; ch += NWG) {
                     float mv[16];
@@ -1137,13 +1164,18 @@ tc_forward_kernel(const TcParams p, const float* __restrict__ x_num, const int* 
                         for (int j = 0; j < 16; ++j) mv[j] = __uint_as_float(mu[j]);
                     } else {
                         uint32_t mh[8];
-                        ptx::tmem_ld8(t_m + ch * 8, mh);
+                        ptx::tmem_ld8(t_m + ch * 8, mh);  // collective: every lane of the warp
                         ptx::tmem_wait_ld8(mh);
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             const float2 mm = __half22float2(*reinterpret_cast<__half2*>(&mh[j]));
                             mv[2 * j] = mm.x;
                             mv[2 * j + 1] = mm.y;
+                        }
+                        if (mrow32) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) mv[j] = mnext[j];
+                            load_mrow(ch + NWG);
                         }
                     }
                     if (agg_tmem) {
