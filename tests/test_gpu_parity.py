@@ -287,3 +287,19 @@ def test_fp32_width_outside_the_tiled_layer(tabnet_mod):
     check("fp32", gpu, O.forward(params, x_num, x_cat))
     with pytest.raises(tabnet_mod.TabnetError):
         tabnet_mod.Model(blob, "bf16x3")
+
+
+def test_wide_model_aggregate_is_summed_in_fp32(tabnet_mod):
+    """At 128 hidden units with a 160-column mask (the 100-input model) TMEM
+    holds the step mask as fp16 pairs; with the masks requested the
+    aggregate is summed from the fp32 mask rows of the output instead.  On
+    4,096 seeded rows in split-bf16 the mean per-row aggregate L1 against
+    float64 is 1.0e-5 that way and 1.45e-4 from the fp16 copies (2^-11 per
+    entry): gated at 4e-5, between the two."""
+    params, blob, x_num, x_cat = synth.load_config("c3", rows=4096)
+    (lg, mk, ag), st = run_gpu(tabnet_mod, blob, "bf16x3", x_num, x_cat)
+    assert st == 0
+    ref = O.forward(params, x_num, x_cat)
+    agg_l1 = np.abs(ag - ref[2]).sum(axis=1)
+    assert agg_l1.mean() <= 4e-5, agg_l1.mean()
+    assert agg_l1.max() <= 2e-2
