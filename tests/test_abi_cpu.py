@@ -79,3 +79,51 @@ def test_create_without_gpu_fails_cleanly(blob):
     assert tabnet.lib().tabnet_create(None, 0, 1, 0, ctypes.byref(h)) == -1
     assert tabnet.lib().tabnet_forward(None, None, None, 1, None, None, None, None) == -1
     assert tabnet.lib().tabnet_status_string(-6) == b"model shape not supported"
+
+
+# The binding's ctypes mirrors of the header's structs, field by field: the
+# same names in the same order, each the size the C type has, so that a
+# field added to one side only (the server's config and statistics grow)
+# fails here rather than shifting every later field on the GPU machine.
+_STRUCTS = {"tabnet_dims": "Dims", "tabnet_segment": "Segment", "tabnet_server_config": "ServerConfig",
+            "tabnet_server_stats": "ServerStats", "tabnet_server_request": "ServerRequest"}
+_C_SIZES = {"int32_t": 4, "int": 4, "double": 8, "uint64_t": 8, "int64_t": 8, "size_t": 8}
+
+
+def _header_structs():
+    src = open(os.path.join(ROOT, "include", "tabnet.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    out = {}
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(\w+)\s*;", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            decl = decl.replace("const ", "")
+            m = re.match(r"(\w+)\s*(\**)\s*(.*)", decl)
+            ctype, stars, names = m.group(1), m.group(2), m.group(3)
+            for nm in names.split(","):
+                nm = nm.strip()
+                ptr = bool(stars) or nm.startswith("*")
+                nm = nm.lstrip("*").strip()
+                fields.append((nm, 8 if ptr else _C_SIZES[ctype]))
+        out[name] = fields
+    return out
+
+
+def test_ctypes_structs_match_the_header():
+    structs = _header_structs()
+    for cname, pyname in _STRUCTS.items():
+        assert cname in structs, cname
+        want = structs[cname]
+        py = getattr(tabnet, pyname)
+        got = [(f[0], ctypes.sizeof(f[1])) for f in py._fields_]
+        assert got == want, (cname, got, want)
+        # natural alignment: the C struct's size
+        off = 0
+        for _, sz in want:
+            off = (off + sz - 1) // sz * sz + sz
+        align = max(sz for _, sz in want)
+        assert ctypes.sizeof(py) == (off + align - 1) // align * align, cname
