@@ -270,7 +270,7 @@ int tabnet_get_tile_config(const tabnet_model* model, int* nwg, int* n_slots, in
  * on one of the model's streams, and forms the next batch without waiting,
  * so requests arriving while others run are admitted as memory frees and
  * overlap on the device.  Latency = completion observed on the host -
- * submission. */
+ * arrival (the submission, or a replayed request's scheduled arrival). */
 typedef struct tabnet_server tabnet_server;
 
 typedef struct {
@@ -307,7 +307,7 @@ typedef struct {
     size_t device_bytes_in_use;
     uint64_t engine_staged;  /* requests whose inputs the engine copied (the input ring
                                 was full when they were submitted) */
-    double p50_queue_ms, p99_queue_ms;  /* of completed requests: submission -> their batch's launch */
+    double p50_queue_ms, p99_queue_ms;  /* of completed requests: arrival -> their batch's launch */
     double engine_busy;      /* fraction of the time since the reset the engine thread was not
                                 asleep waiting for work */
     double engine_max_pass_ms;  /* longest single engine pass (completions + launches) */
